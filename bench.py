@@ -1,0 +1,424 @@
+"""Benchmark: discriminate + millisecond-histogram one paper-scale day on GB300.
+
+Default workload: 400 M time-sorted session records (diurnal 3:1 rate, +-500 ms
+jitter), 2,000 CIDR prefixes /8-/30, 1 ms bins over 24 h (86.4 M bins x 2
+directions). A step = zero the histogram + one fused discriminate/histogram
+pass over all records (inputs resident in HBM; 8 GB of records, far larger
+than L2). The plain discriminate -> radix sort -> reduce-by-key path is timed
+on the same data for comparison, and ``e2e`` times the same step through the
+public API with the records copied from pinned host memory and the histogram
+copied back every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload day|heavy|tiny]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+
+METRIC = "sessions/sec (bit-exact) and HBM GB/s vs peak, fused vs sort+reduce on 1 GB300"
+UNIT = "sessions/s"
+RECORD_BYTES = 20   # ts u64 + src u32 + dst u32 + bytes u32
+BIN_BYTES = 24      # 2 directions x (u32 count + u64 byte sum)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="day", choices=sorted(gen.WORKLOADS))
+    ap.add_argument("--records", type=int, default=0, help="override the record count")
+    ap.add_argument("--strategy", default="tune",
+                    help="tune | global_atomic | priv_tile | atomic_noagg | sort_reduce")
+    ap.add_argument("--plain-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, rank):
+    w = gen.WORKLOADS[args.workload]
+    if args.records:
+        w = gen.scaled(w, args.records)
+    return w
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_12863_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = dict(kv.split("=", 1) for kv in line.split())
+            if parts.get("kernel") == kernel and parts.get("workload") == workload \
+                    and parts.get("source") == cur:
+                return float(parts["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(index), "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        self.window = (None, None)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, start: bool):
+        t = time.time()
+        a, b = self.window
+        self.window = (t, b) if start else (a, t)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        a, b = self.window
+        rows = [ln for t, ln in self.lines if a is not None and a - 0.15 <= t <= b + 0.15]
+        if not rows:
+            rows = [ln for _, ln in self.lines[-3:]]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, seconds: float):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+
+    o = oracle.get()
+    net, ln = gen.make_table(w.table, w.seed)
+    mid = w.records.n // 2
+    probe = min(100_000, w.records.n)
+    rec = gen.make_records(w.records, w.seed, net, ln, first=mid - probe // 2, n=probe)
+    t = time.perf_counter()
+    o.discriminate_histogram(net, ln, rec, w.t0, w.bin_width, min(w.n_bins, 1 << 27))
+    dt = time.perf_counter() - t
+    m = int(min(w.records.n, max(probe, probe * seconds / max(dt, 1e-6))))
+    rec = gen.make_records(w.records, w.seed, net, ln, first=max(0, mid - m // 2), n=m)
+    t = time.perf_counter()
+    o.discriminate_histogram(net, ln, rec, w.t0, w.bin_width, w.n_bins)
+    dt = time.perf_counter() - t
+    return {"value": m / dt, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
+            "sample": f"{m} contiguous records from the middle of the {w.name} workload, "
+                      f"full {w.table.n}-prefix table, {w.n_bins} bins; {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    o = oracle.get()
+    w = workload(args, rank)
+    net, ln = gen.make_table(w.table, w.seed)
+    # size each step's sample so that all warm-up + timed steps fit ~2.5 minutes
+    per_step = max(0.05, 150.0 / (args.steps + args.warmup))
+    probe = min(50_000, w.records.n)
+    rec = gen.make_records(w.records, w.seed, net, ln, n=probe)
+    t = time.perf_counter()
+    o.discriminate_histogram(net, ln, rec, w.t0, w.bin_width, w.n_bins)
+    dt = time.perf_counter() - t
+    m = int(min(w.records.n, max(1000, probe * per_step / max(dt, 1e-6))))
+    samples = []
+    for s in range(args.warmup + args.steps):
+        first = (s * m) % max(1, w.records.n - m)
+        rec = gen.make_records(w.records, w.seed, net, ln, first=first, n=m)
+        t = time.perf_counter()
+        o.discriminate_histogram(net, ln, rec, w.t0, w.bin_width, w.n_bins)
+        if s >= args.warmup:
+            samples.append(time.perf_counter() - t)
+    total = sum(samples)
+    value = m * len(samples) / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(samples),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "records_per_step": m, "prefixes": w.table.n,
+                       "n_bins": w.n_bins},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
+                             "sample": f"{m} records of {w.name} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2106_12863_gb300 as sinet
+
+    sinet.load()  # fails loudly without the CUDA library
+
+    w = workload(args, rank)
+    n = w.records.n
+    seed = w.seed + rank  # weak scaling: every rank processes its own day
+    net, ln = gen.make_table(w.table, w.seed)
+    # records generated straight into pinned host memory, then made resident
+    h = {"ts": torch.empty(n, dtype=torch.int64, pin_memory=True),
+         "src": torch.empty(n, dtype=torch.int32, pin_memory=True),
+         "dst": torch.empty(n, dtype=torch.int32, pin_memory=True),
+         "bytes": torch.empty(n, dtype=torch.int32, pin_memory=True)}
+    tg = time.perf_counter()
+    gen.fill_records(w.records, seed, net, ln, 0, n, h["ts"], h["src"], h["dst"], h["bytes"])
+    t_gen = time.perf_counter() - tg
+    d = {k: v.to(dev) for k, v in h.items()}
+    table = sinet.PrefixTable(net, ln)
+    out = sinet.Histogram(w.n_bins, dev, zero=False)
+    stream = torch.cuda.current_stream(dev)
+    hints = sinet.HINT_TIME_SORTED if w.records.ts_kind == "diurnal" else 0
+
+    def params(strategy, accumulate=True):
+        return sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy=strategy, hints=hints,
+                                accumulate=accumulate)
+
+    def zero():
+        out.count.zero_()
+        out.bytes.zero_()
+        out.stats.zero_()
+
+    def step(strategy):
+        zero()
+        sinet.discriminate_histogram(table, d["ts"], d["src"], d["dst"], d["bytes"],
+                                     params(strategy), out)
+
+    # autotune: one untimed run of each candidate, keep the fastest
+    cands = ["priv_tile", "global_atomic", "atomic_noagg"] if args.strategy == "tune" else [args.strategy]
+    tune = {}
+    for c in cands:
+        step(c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tune[c] = e0.elapsed_time(e1)
+    strategy = min(tune, key=tune.get)
+
+    for _ in range(args.warmup):
+        step(strategy)
+    torch.cuda.synchronize()
+    # timed region: K steps, zero + fused kernel, events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.mark(True)
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_begin.record(stream)
+    for i in range(args.steps):
+        a, b, c = ev[i]
+        a.record(stream)
+        zero()
+        b.record(stream)
+        sinet.discriminate_histogram(table, d["ts"], d["src"], d["dst"], d["bytes"],
+                                     params(strategy), out)
+        c.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.mark(False)
+    clk = clocks.stop()
+    total_ms = t_begin.elapsed_time(t_end)
+    kern_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    zero_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms / 1e3)
+    stats = out.stats.cpu().numpy().view(np.uint64)
+    # invariant spot check on the last step: every record classified once
+    assert int(stats[:4].sum()) == n, "class counts do not sum to the record count"
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+              "data": "synthetic (seeded generator; paper-shaped day)"}
+    alg_bytes = RECORD_BYTES * n + BIN_BYTES * w.n_bins
+    peak, peak_kind = peaks()
+    kname = {"priv_tile": "k_fused_tile", "global_atomic": "k_fused_atomic",
+             "atomic_noagg": "k_fused_atomic", "sort_reduce": "k_radix_pass"}[strategy]
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "traffic": recorded_traffic(kname, w.name),
+                          "kernel": kname, "peak_kind": peak_kind,
+                          "algorithmic_bytes_per_launch": alg_bytes,
+                          "kernel_ms": kern_ms, "zero_ms": zero_ms,
+                          "step_frac": alg_bytes / (ms_per_step / 1e3) / 1e9 / peak}
+    result["gpu_launches"] = args.steps  # one fused kernel per step (zeroing is cudaMemset)
+    result["config"] = {"workload": w.name, "records": n, "prefixes": w.table.n,
+                        "n_bins": w.n_bins, "bin_width_ms": w.bin_width, "strategy": strategy,
+                        "tune_ms": tune, "l2": f"inputs larger than L2 ({RECORD_BYTES * n / 1e9:.1f} GB of records)",
+                        "policy": "exclusive", "parallelism": f"replicas x{world} (weak)",
+                        "gen_s": round(t_gen, 1)}
+    result["clocks"] = clk
+
+    # the plain path (paper's structure) on the same data
+    if not args.no_plain:
+        for _ in range(2):
+            step("sort_reduce")
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.plain_steps):
+            step("sort_reduce")
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1) / args.plain_steps
+        result["plain_sort_reduce"] = {"value": n / (plain_ms / 1e3), "unit": UNIT,
+                                       "ms_per_step": plain_ms, "steps": args.plain_steps}
+        result["fused_vs_plain"] = (n / (ms_per_step / 1e3)) / result["plain_sort_reduce"]["value"]
+
+    # end to end through the public API: pinned host records in, histogram out
+    if not args.no_e2e:
+        hout = {"count": torch.empty((2, w.n_bins), dtype=torch.int32, pin_memory=True),
+                "bytes": torch.empty((2, w.n_bins), dtype=torch.int64, pin_memory=True),
+                "stats": torch.empty(8, dtype=torch.int64, pin_memory=True)}
+
+        def e2e_step():
+            for k in d:
+                d[k].copy_(h[k], non_blocking=True)
+            sinet.discriminate_histogram(table, d["ts"], d["src"], d["dst"], d["bytes"],
+                                         params(strategy, accumulate=False), out)
+            hout["count"].copy_(out.count, non_blocking=True)
+            hout["bytes"].copy_(out.bytes, non_blocking=True)
+            hout["stats"].copy_(out.stats, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        q1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = q0.elapsed_time(q1) / args.e2e_steps
+        h2d = sum(v.numel() * v.element_size() for v in h.values())
+        d2h = sum(v.numel() * v.element_size() for v in hout.values())
+        result["e2e"] = {"value": world * n / (e2e_ms / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                         "ms_per_step": e2e_ms, "steps": args.e2e_steps}
+        st2 = hout["stats"].numpy().view(np.uint64)
+        assert np.array_equal(st2, stats), "e2e result differs from the resident run"
+
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    table.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

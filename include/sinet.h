@@ -1,0 +1,219 @@
+/*
+ * sinet.h - C ABI of the GB300 session discrimination + histogram library.
+ *
+ * The method (arXiv 2106.12863):
+ *   - Algorithm 1 ("session ingoing/outgoing discrimination"): for a CIDR
+ *     entry Y/Z and an address X, SB = bitmask(X, Z), CB = bitmask(Y, Z),
+ *     and a zero SB - CB is a match. bitmask keeps the top Z bits of the
+ *     32-bit address (Fig. 4). The input is a CIDR list; an address is inside
+ *     when any entry matches.
+ *   - Section 5 ("Pairwise Reduction Pattern with GPU", "Merge Scatter
+ *     Pattern with CPU"): the discriminated sessions are histogrammed into
+ *     <timestamp, count> and <timestamp, bytes> maps at millisecond
+ *     granularity (86,400,000 bins per day), one per direction.
+ *
+ * Conventions shared by every entry point:
+ *   - Addresses are uint32 with the first octet most significant
+ *     (192.168.1.5 == 0xC0A80105).
+ *   - Records are structure-of-arrays: ts_ms uint64[n], src uint32[n],
+ *     dst uint32[n], bytes uint32[n] (Table 1 fields capture_time,
+ *     source_ip, destination_ip, bytes). Record and output pointers are
+ *     DEVICE pointers owned by the caller, each aligned to its element size;
+ *     16-byte alignment lets the kernels use 128-bit loads.
+ *   - class of a record = src_in | dst_in << 1: 0 neither, 1 source inside
+ *     (outgoing), 2 destination inside (ingoing), 3 both.
+ *   - Direction index d: 0 = outgoing (egress), 1 = ingoing (ingress).
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream).
+ *     SINET_OK means validated and enqueued. Host-detectable errors return
+ *     before anything is launched. Device-side failures (a bounded wait that
+ *     ran out, a failed bounds check in a checked build) are latched in a
+ *     per-device status word read by sinet_device_status().
+ *   - Nothing aborts, prints or traps. Library-owned scratch comes from
+ *     stream-ordered cudaMallocAsync and is released on the same stream.
+ *   - Limits: n <= 2^40 records, 1 <= n_bins <= 2^31 - 1, bin width >= 1,
+ *     t0 + n_bins * bin_width must fit in uint64, prefix length <= 32.
+ */
+#ifndef SINET_H
+#define SINET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the runtime's type is this same pointer). */
+typedef struct CUstream_st *sinet_stream_t;
+
+typedef enum {
+    SINET_OK = 0,
+    SINET_ERR_INVALID_ARG = 1,     /* bad pointer, size, length or parameter */
+    SINET_ERR_CUDA = 2,            /* a CUDA runtime call failed; see sinet_last_cuda_error() */
+    SINET_ERR_OOM = 3,             /* device allocation failed */
+    SINET_ERR_BUDGET = 4,          /* a request does not fit the caller's memory budget */
+    SINET_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out */
+    SINET_ERR_TABLE_TOO_LARGE = 6, /* more prefixes than the table format holds */
+    SINET_ERR_DEVICE_CHECK = 7,    /* a device-side bounds check failed (checked builds) */
+    SINET_ERR_UNSUPPORTED = 8      /* option combination not available */
+} sinet_status;
+
+/* How the histogram update is carried out. All give identical results. */
+typedef enum {
+    SINET_STRAT_AUTO = 0,          /* autotuner / heuristics choose */
+    SINET_STRAT_GLOBAL_ATOMIC = 1, /* warp match + reduce, then global atomics */
+    SINET_STRAT_PRIV_TILE = 2,     /* shared-memory bin tile per chunk (time-sorted input) */
+    SINET_STRAT_SORT_REDUCE = 3,   /* plain path: discriminate, radix sort, reduce by key */
+    SINET_STRAT_SMEM_FULL = 4,     /* whole histogram privatised in shared memory (small n_bins) */
+    SINET_STRAT_ATOMIC_NOAGG = 5   /* global atomics without warp aggregation */
+} sinet_strategy;
+
+/* How membership is looked up. Both are exact. */
+typedef enum {
+    SINET_LOOKUP_AUTO = 0,
+    SINET_LOOKUP_INTERVAL = 1, /* merged disjoint intervals + top-k-bit direct index */
+    SINET_LOOKUP_PML = 2       /* per-mask-length binary search over canonical networks */
+} sinet_lookup;
+
+/* Direction bits used in sinet_hist_params.policy. */
+#define SINET_DIR_OUT 1u
+#define SINET_DIR_IN 2u
+
+/* Input hints (sinet_hist_params.hints). */
+#define SINET_HINT_TIME_SORTED 1u  /* records are (nearly) sorted by ts */
+
+typedef struct {
+    uint64_t t0_ms;        /* window start */
+    uint64_t bin_width_ms; /* >= 1 */
+    uint64_t n_bins;       /* window = [t0, t0 + n_bins * bin_width) */
+    uint8_t policy[4];     /* class -> direction bits; exclusive default {0, OUT, IN, 0} */
+    int32_t accumulate;    /* 0: outputs and stats are overwritten; 1: added to */
+    int32_t strategy;      /* sinet_strategy */
+    int32_t lookup;        /* sinet_lookup */
+    uint32_t hints;        /* SINET_HINT_* */
+    uint32_t tile_bins;    /* PRIV_TILE bins per direction per tile (0 = default) */
+    uint32_t block_threads;/* threads per CTA (0 = default) */
+} sinet_hist_params;
+
+/*
+ * Histogram outputs, caller-owned device arrays:
+ *   count[d]: uint32[n_bins]  (sessions per bin; wraps modulo 2^32 when accumulating)
+ *   bytes[d]: uint64[n_bins]  (sum of the records' bytes field)
+ *   stats:    uint64[8]       (records per class [0..3], out-of-window records per
+ *                              routed direction [4..5], reserved [6..7])
+ * A record routed to direction d whose ts lies outside the window is not
+ * binned; it is counted in stats[4 + d].
+ */
+typedef struct {
+    uint32_t *count[2];
+    uint64_t *bytes[2];
+    uint64_t *stats;
+} sinet_hist_out;
+
+/* Opaque, library-owned, device-resident compiled CIDR list. */
+typedef struct sinet_prefix_table sinet_prefix_table;
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+uint32_t sinet_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *sinet_status_string(sinet_status s);
+
+/* The last CUDA error code seen by this thread (0 if none). */
+int sinet_last_cuda_error(void);
+
+/*
+ * Parse "a.b.c.d/z" (or "a.b.c.d", meaning /32) into net and len. Host only.
+ * The CIDR notation Y.Y.Y.Y/Z of Algorithm 1. Host bits are kept as written.
+ * Returns SINET_ERR_INVALID_ARG on malformed text or z > 32.
+ */
+sinet_status sinet_parse_cidr(const char *text, uint32_t *net, uint8_t *len);
+
+/*
+ * Compile a CIDR list on the host (no CUDA call) and report the derived
+ * structures. Entries are canonicalised (net &= bitmask(len), the CB of
+ * Algorithm 1), deduplicated and grouped by mask length; the union of all
+ * entries is also emitted as sorted, disjoint, non-adjacent closed intervals
+ * [lo, hi], with a direct index over the top `index_bits` address bits:
+ * index[b] = first interval whose hi >= b << (32 - index_bits); the interval
+ * that can hold an address of bucket b is among index[b] .. index[b + 1].
+ *
+ *   h_net, h_len  host arrays of n entries (len <= 32)
+ *   index_bits    0..20 (0 = choose: as many bits as fit a shared-memory budget)
+ *   nets_by_len   out, capacity n: canonical unique networks, ascending length,
+ *                 sorted within each length (may be NULL)
+ *   len_offset    out, uint32[34]: length L occupies [len_offset[L], len_offset[L+1])
+ *   iv_lo, iv_hi  out, capacity n: the intervals (may be NULL)
+ *   index         out, capacity 2^index_bits + 1 (may be NULL)
+ *   counts        out, uint32[4]: unique entries, intervals, index bits used,
+ *                 largest candidate range of a bucket
+ * Returns SINET_ERR_INVALID_ARG for a length > 32, a NULL required pointer,
+ * or index_bits > 20; SINET_ERR_TABLE_TOO_LARGE for n > 2^24.
+ */
+sinet_status sinet_compile_prefix_table(const uint32_t *h_net, const uint8_t *h_len, uint32_t n,
+                                        uint32_t index_bits, uint32_t *nets_by_len,
+                                        uint32_t *len_offset, uint32_t *iv_lo, uint32_t *iv_hi,
+                                        uint32_t *index, uint32_t *counts);
+
+/*
+ * Compile a CIDR list (as sinet_compile_prefix_table) and upload it to the
+ * current device on `stream`. The table is owned by the library until
+ * sinet_destroy_prefix_table. An empty list (n == 0) is valid: nothing is
+ * inside. h_net/h_len are host arrays and are not retained.
+ */
+sinet_status sinet_build_prefix_table(const uint32_t *h_net, const uint8_t *h_len, uint32_t n,
+                                      sinet_stream_t stream, sinet_prefix_table **out);
+
+/* Free a table (synchronises the device it lives on). NULL is a no-op. */
+sinet_status sinet_destroy_prefix_table(sinet_prefix_table *t);
+
+/*
+ * Algorithm 1 per record: class[i] = in(src[i]) | in(dst[i]) << 1.
+ *   d_class         device uint8[n], may be NULL (counts only)
+ *   d_class_counts  device uint64[4], overwritten with records per class
+ *   lookup          sinet_lookup
+ * n == 0 writes zero counts.
+ */
+sinet_status sinet_discriminate(const sinet_prefix_table *t, const uint32_t *d_src,
+                                const uint32_t *d_dst, uint64_t n, uint8_t *d_class,
+                                uint64_t *d_class_counts, int32_t lookup, sinet_stream_t stream);
+
+/*
+ * Histogram of already-classified records (Section 5's map-reduce step):
+ * every record routed by p->policy[class] to direction d lands in bin
+ * (ts - t0) / w of count[d] / bytes[d], or in stats[4 + d] when outside the
+ * window. stats[0..3] count the classes seen. Classes must be 0..3
+ * (values above 3 use their low two bits).
+ */
+sinet_status sinet_histogram(const uint64_t *d_ts, const uint32_t *d_bytes, const uint8_t *d_class,
+                             uint64_t n, const sinet_hist_params *p, const sinet_hist_out *o,
+                             sinet_stream_t stream);
+
+/*
+ * Fused Algorithm 1 + histogram in one pass over the records (the hot path).
+ * p->strategy selects the update scheme (SINET_STRAT_SORT_REDUCE runs the
+ * plain discriminate -> radix sort -> reduce-by-key path). Output as in
+ * sinet_histogram.
+ */
+sinet_status sinet_discriminate_histogram(const sinet_prefix_table *t, const uint64_t *d_ts,
+                                          const uint32_t *d_src, const uint32_t *d_dst,
+                                          const uint32_t *d_bytes, uint64_t n,
+                                          const sinet_hist_params *p, const sinet_hist_out *o,
+                                          sinet_stream_t stream);
+
+/*
+ * Read and clear the device status word of the current device, after
+ * synchronising `stream`. *device_code receives the latched sinet_status
+ * (SINET_OK if nothing failed).
+ */
+sinet_status sinet_device_status(sinet_stream_t stream, uint32_t *device_code);
+
+/* Fill a params struct with defaults: exclusive policy, AUTO strategy/lookup. */
+void sinet_default_params(sinet_hist_params *p, uint64_t t0_ms, uint64_t bin_width_ms,
+                          uint64_t n_bins);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SINET_H */

@@ -1,0 +1,471 @@
+// C ABI: argument validation, table upload, strategy dispatch, scratch.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "launch.h"
+#include "table_host.h"
+
+struct sinet_prefix_table {
+    int device;
+    sinet::TableHost host;
+    sinet::TableImage img;
+    uint8_t *d_image;
+    sinet::TableArgs args;
+};
+
+namespace sinet {
+
+struct DeviceState {
+    bool ready = false;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    uint32_t *status = nullptr;  // device status word
+};
+
+static std::mutex g_mu;
+static DeviceState g_dev[64];
+static thread_local int t_last_cuda = 0;
+
+static sinet_status cuda_fail(cudaError_t e) {
+    t_last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? SINET_ERR_OOM : SINET_ERR_CUDA;
+}
+
+#define SINET_CUDA(x)                                   \
+    do {                                                \
+        cudaError_t e_ = (x);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_);    \
+    } while (0)
+
+static sinet_status device_state(DeviceState **out) {
+    int dev = 0;
+    SINET_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SINET_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &d = g_dev[dev];
+    if (!d.ready) {
+        int v = 0;
+        SINET_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        d.sm_count = v;
+        SINET_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        d.smem_optin = (size_t)v;
+        SINET_CUDA(cudaMalloc(&d.status, 256));
+        SINET_CUDA(cudaMemset(d.status, 0, 256));
+        d.ready = true;
+    }
+    *out = &d;
+    return SINET_OK;
+}
+
+// Host side of the invariant-integer divider (Granlund & Montgomery 1994).
+static Divider make_divider(uint64_t w) {
+    Divider d{};
+    uint32_t l = 0;
+    while (l < 64 && (((unsigned __int128)1) << l) < w) l++;
+    const unsigned __int128 two64 = ((unsigned __int128)1) << 64;
+    d.m = (uint64_t)((two64 * ((((unsigned __int128)1) << l) - w)) / w + 1);
+    d.sh1 = l < 1 ? l : 1;
+    d.sh2 = l >= 1 ? l - 1 : 0;
+    return d;
+}
+
+// Quad geometry: pick the first record index (<= 0) at which every stream is
+// 16-byte aligned (4-byte for byte streams), or fall back to scalar loads.
+struct Stream {
+    const void *p;
+    uint32_t esize;
+};
+static QuadGeom make_geom(uint64_t n, std::initializer_list<Stream> streams) {
+    QuadGeom g{};
+    g.n = n;
+    g.shift = 0;
+    g.vec = 0;
+    for (int s = 0; s >= -3; --s) {
+        bool ok = true;
+        for (const Stream &st : streams) {
+            if (!st.p) continue;
+            const uint64_t a = (uint64_t)(uintptr_t)st.p + (uint64_t)((int64_t)s * (int64_t)st.esize);
+            const uint64_t al = st.esize == 1 ? 4 : 16;
+            if (a % al) ok = false;
+        }
+        if (ok) {
+            g.shift = s;
+            g.vec = 1;
+            break;
+        }
+    }
+    g.quads = n == 0 ? 0 : (n + (uint64_t)(-g.shift) + 3) / 4;
+    return g;
+}
+
+static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static const uint64_t kMaxN = 1ull << 40;
+
+static sinet_status check_params(const sinet_hist_params *p) {
+    if (!p) return SINET_ERR_INVALID_ARG;
+    if (p->bin_width_ms == 0 || p->n_bins == 0 || p->n_bins > 0x7FFFFFFFull) return SINET_ERR_INVALID_ARG;
+    const unsigned __int128 end = (unsigned __int128)p->t0_ms + (unsigned __int128)p->n_bins * p->bin_width_ms;
+    if (end > (unsigned __int128)UINT64_MAX) return SINET_ERR_INVALID_ARG;
+    for (int c = 0; c < 4; ++c)
+        if (p->policy[c] > 3) return SINET_ERR_INVALID_ARG;
+    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_ATOMIC_NOAGG) return SINET_ERR_INVALID_ARG;
+    if (p->lookup < SINET_LOOKUP_AUTO || p->lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
+    if (p->block_threads && (p->block_threads > 256 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
+    return SINET_OK;
+}
+
+static sinet_status check_out(const sinet_hist_out *o) {
+    if (!o || !o->count[0] || !o->count[1] || !o->bytes[0] || !o->bytes[1] || !o->stats)
+        return SINET_ERR_INVALID_ARG;
+    if (!aligned(o->count[0], 4) || !aligned(o->count[1], 4) || !aligned(o->bytes[0], 8) ||
+        !aligned(o->bytes[1], 8) || !aligned(o->stats, 8))
+        return SINET_ERR_INVALID_ARG;
+    return SINET_OK;
+}
+
+static HistArgs make_hist(const sinet_hist_params *p, const sinet_hist_out *o) {
+    HistArgs h{};
+    h.cnt[0] = o->count[0];
+    h.cnt[1] = o->count[1];
+    h.byt[0] = o->bytes[0];
+    h.byt[1] = o->bytes[1];
+    h.stats = o->stats;
+    h.t0 = p->t0_ms;
+    h.span = p->n_bins * p->bin_width_ms;
+    h.div = make_divider(p->bin_width_ms);
+    h.w_is_one = p->bin_width_ms == 1;
+    h.policy = 0;
+    h.two_dir = 0;
+    for (int c = 0; c < 4; ++c) {
+        h.policy |= (uint32_t)p->policy[c] << (8 * c);
+        if (p->policy[c] == 3) h.two_dir = 1;
+    }
+    h.n_bins = (uint32_t)p->n_bins;
+    return h;
+}
+
+static sinet_status zero_outputs(const sinet_hist_params *p, const sinet_hist_out *o, cudaStream_t s) {
+    if (p->accumulate) return SINET_OK;
+    SINET_CUDA(cudaMemsetAsync(o->count[0], 0, 4 * p->n_bins, s));
+    SINET_CUDA(cudaMemsetAsync(o->count[1], 0, 4 * p->n_bins, s));
+    SINET_CUDA(cudaMemsetAsync(o->bytes[0], 0, 8 * p->n_bins, s));
+    SINET_CUDA(cudaMemsetAsync(o->bytes[1], 0, 8 * p->n_bins, s));
+    SINET_CUDA(cudaMemsetAsync(o->stats, 0, 64, s));
+    return SINET_OK;
+}
+
+// Lookup form for a table: the staged interval form when it fits shared
+// memory, the per-length form on request, else global-memory intervals.
+static int pick_lookup(const sinet_prefix_table *t, int32_t lookup, sinet_status *err) {
+    *err = SINET_OK;
+    if (lookup == SINET_LOOKUP_PML) {
+        if (!t->img.pml_fits_smem) *err = SINET_ERR_UNSUPPORTED;
+        return LK_PML;
+    }
+    return t->img.iv_fits_smem ? LK_INTERVAL : LK_INTERVAL_GLOBAL;
+}
+
+static uint32_t table_smem(const sinet_prefix_table *t, int lk) {
+    if (!t) return 0;
+    if (lk == LK_INTERVAL) return t->img.iv_bytes;
+    if (lk == LK_PML) return t->img.pml_bytes;
+    return 0;
+}
+
+// Shared-memory budget left for a bin tile after the staged table (and the
+// kernel's static shared memory).
+static uint32_t tile_capacity(const DeviceState *ds, uint32_t tsm) {
+    const size_t reserve = 1024;
+    const size_t used = ((tsm + 15u) & ~15u) + reserve;
+    if (ds->smem_optin <= used) return 0;
+    return (uint32_t)((ds->smem_optin - used) / 24);
+}
+
+// The histogram step for every strategy (records already validated).
+static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs &r,
+                             const sinet_hist_params *p, const sinet_hist_out *o, cudaStream_t s) {
+    DeviceState *ds = nullptr;
+    sinet_status st = device_state(&ds);
+    if (st != SINET_OK) return st;
+    HistArgs h = make_hist(p, o);
+    TableArgs ta_tab{};
+    if (t) ta_tab = t->args;
+    LaunchCfg c;
+    c.block = p->block_threads ? (int)p->block_threads : 256;
+    c.stream = s;
+    c.status = ds->status;
+    c.sm_count = ds->sm_count;
+    const uint32_t tsm = table_smem(t, lk);
+    const uint32_t cap = tile_capacity(ds, tsm);
+
+    int strat = p->strategy;
+    if (strat == SINET_STRAT_AUTO) {
+        if (2ull * p->n_bins <= 8192 && p->n_bins <= cap)
+            strat = SINET_STRAT_SMEM_FULL;
+        else if (p->hints & SINET_HINT_TIME_SORTED)
+            strat = SINET_STRAT_PRIV_TILE;
+        else
+            strat = SINET_STRAT_GLOBAL_ATOMIC;
+    }
+    st = zero_outputs(p, o, s);
+    if (st != SINET_OK) return st;
+    if (r.g.n == 0) return SINET_OK;
+    cudaError_t e = cudaSuccess;
+    switch (strat) {
+        case SINET_STRAT_GLOBAL_ATOMIC:
+            e = run_fused_atomic(lk, true, r, ta_tab, h, c);
+            break;
+        case SINET_STRAT_ATOMIC_NOAGG:
+            e = run_fused_atomic(lk, false, r, ta_tab, h, c);
+            break;
+        case SINET_STRAT_PRIV_TILE:
+        case SINET_STRAT_SMEM_FULL: {
+            TileArgs ta{};
+            if (strat == SINET_STRAT_SMEM_FULL) {
+                if (p->n_bins > cap) return SINET_ERR_UNSUPPORTED;
+                ta.tile_bins = (uint32_t)p->n_bins;
+                ta.full = 1;
+                ta.iters = 16;
+                ta.margin = 0;
+            } else {
+                uint32_t T = p->tile_bins ? p->tile_bins : 4096;
+                if (T > cap) T = cap & ~255u;
+                if (T == 0) return SINET_ERR_UNSUPPORTED;
+                ta.tile_bins = T;
+                ta.full = 0;
+                ta.iters = 8;
+                ta.margin = T / 8;
+            }
+            e = run_fused_tile(lk, r, ta_tab, h, ta, c);
+            break;
+        }
+        case SINET_STRAT_SORT_REDUCE: {
+            if (r.g.n * (h.two_dir ? 2ull : 1ull) >= 0xFFFFFFF0ull) return SINET_ERR_UNSUPPORTED;
+            SortPlan plan = plan_sort_reduce(r.g.n, h.n_bins, h.two_dir);
+            void *scratch = nullptr;
+            e = cudaMallocAsync(&scratch, plan.scratch_bytes, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            e = run_sort_reduce(lk, r, ta_tab, h, plan, scratch, p->accumulate != 0, c);
+            cudaError_t e2 = cudaFreeAsync(scratch, s);
+            if (e == cudaSuccess) e = e2;
+            break;
+        }
+        default:
+            return SINET_ERR_INVALID_ARG;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    return SINET_OK;
+}
+
+}  // namespace sinet
+
+using namespace sinet;
+
+extern "C" {
+
+uint32_t sinet_version(void) { return 0x000100u; }
+
+const char *sinet_status_string(sinet_status s) {
+    switch (s) {
+        case SINET_OK: return "ok";
+        case SINET_ERR_INVALID_ARG: return "invalid argument";
+        case SINET_ERR_CUDA: return "CUDA error";
+        case SINET_ERR_OOM: return "out of device memory";
+        case SINET_ERR_BUDGET: return "over memory budget";
+        case SINET_ERR_TIMEOUT: return "device-side wait timed out";
+        case SINET_ERR_TABLE_TOO_LARGE: return "prefix table too large";
+        case SINET_ERR_DEVICE_CHECK: return "device-side check failed";
+        case SINET_ERR_UNSUPPORTED: return "unsupported option combination";
+    }
+    return "unknown status";
+}
+
+int sinet_last_cuda_error(void) { return t_last_cuda; }
+
+void sinet_default_params(sinet_hist_params *p, uint64_t t0_ms, uint64_t bin_width_ms, uint64_t n_bins) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->t0_ms = t0_ms;
+    p->bin_width_ms = bin_width_ms;
+    p->n_bins = n_bins;
+    p->policy[0] = 0;
+    p->policy[1] = SINET_DIR_OUT;
+    p->policy[2] = SINET_DIR_IN;
+    p->policy[3] = 0;
+}
+
+sinet_status sinet_parse_cidr(const char *text, uint32_t *net, uint8_t *len) {
+    if (!text || !net || !len) return SINET_ERR_INVALID_ARG;
+    uint32_t oct[4];
+    const char *s = text;
+    for (int i = 0; i < 4; ++i) {
+        if (*s < '0' || *s > '9') return SINET_ERR_INVALID_ARG;
+        uint32_t v = 0;
+        int digits = 0;
+        while (*s >= '0' && *s <= '9') {
+            v = v * 10 + (uint32_t)(*s - '0');
+            if (++digits > 3 || v > 255) return SINET_ERR_INVALID_ARG;
+            ++s;
+        }
+        oct[i] = v;
+        if (i < 3) {
+            if (*s != '.') return SINET_ERR_INVALID_ARG;
+            ++s;
+        }
+    }
+    uint32_t z = 32;
+    if (*s == '/') {
+        ++s;
+        if (*s < '0' || *s > '9') return SINET_ERR_INVALID_ARG;
+        z = 0;
+        int digits = 0;
+        while (*s >= '0' && *s <= '9') {
+            z = z * 10 + (uint32_t)(*s - '0');
+            if (++digits > 2) return SINET_ERR_INVALID_ARG;
+            ++s;
+        }
+        if (z > 32) return SINET_ERR_INVALID_ARG;
+    }
+    if (*s != '\0') return SINET_ERR_INVALID_ARG;
+    *net = oct[0] << 24 | oct[1] << 16 | oct[2] << 8 | oct[3];
+    *len = (uint8_t)z;
+    return SINET_OK;
+}
+
+sinet_status sinet_build_prefix_table(const uint32_t *h_net, const uint8_t *h_len, uint32_t n,
+                                      sinet_stream_t stream, sinet_prefix_table **out) {
+    if (!out) return SINET_ERR_INVALID_ARG;
+    *out = nullptr;
+    sinet_prefix_table *t = new (std::nothrow) sinet_prefix_table();
+    if (!t) return SINET_ERR_OOM;
+    int rc = compile_table(h_net, h_len, n, 0, t->host);
+    if (rc != SINET_OK) {
+        delete t;
+        return (sinet_status)rc;
+    }
+    std::vector<uint8_t> buf = serialise(t->host, t->img);
+    cudaError_t e = cudaGetDevice(&t->device);
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_image, buf.size());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->d_image, buf.data(), buf.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // host buffer goes out of scope
+    if (e != cudaSuccess) {
+        if (t->d_image) cudaFree(t->d_image);
+        delete t;
+        return cuda_fail(e);
+    }
+    TableArgs &a = t->args;
+    a.image = t->d_image;
+    a.iv_bytes = t->img.iv_bytes;
+    a.off_lo = t->img.off_lo;
+    a.off_hi = t->img.off_hi;
+    a.off_idx16 = t->img.off_idx16;
+    a.off_idx32 = t->img.off_idx32;
+    a.n_iv = (uint32_t)t->host.lo.size();
+    a.index_bits = t->host.index_bits;
+    a.off_nets = t->img.off_nets;
+    a.off_groups = t->img.off_groups;
+    a.pml_bytes = t->img.pml_bytes;
+    a.n_groups = (uint32_t)t->host.groups.size();
+    *out = t;
+    return SINET_OK;
+}
+
+sinet_status sinet_destroy_prefix_table(sinet_prefix_table *t) {
+    if (!t) return SINET_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaError_t e = cudaSuccess;
+    if (cur != t->device) cudaSetDevice(t->device);
+    e = cudaDeviceSynchronize();
+    if (t->d_image) {
+        cudaError_t e2 = cudaFree(t->d_image);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (cur != t->device) cudaSetDevice(cur);
+    delete t;
+    return e == cudaSuccess ? SINET_OK : cuda_fail(e);
+}
+
+sinet_status sinet_discriminate(const sinet_prefix_table *t, const uint32_t *d_src, const uint32_t *d_dst,
+                                uint64_t n, uint8_t *d_class, uint64_t *d_class_counts, int32_t lookup,
+                                sinet_stream_t stream) {
+    if (!t || !d_class_counts || !aligned(d_class_counts, 8)) return SINET_ERR_INVALID_ARG;
+    if (n > kMaxN) return SINET_ERR_INVALID_ARG;
+    if (n && (!d_src || !d_dst || !aligned(d_src, 4) || !aligned(d_dst, 4))) return SINET_ERR_INVALID_ARG;
+    if (lookup < SINET_LOOKUP_AUTO || lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    sinet_status st = device_state(&ds);
+    if (st != SINET_OK) return st;
+    const int lk = pick_lookup(t, lookup, &st);
+    if (st != SINET_OK) return st;
+    SINET_CUDA(cudaMemsetAsync(d_class_counts, 0, 32, stream));
+    if (n == 0) return SINET_OK;
+    RecArgs r{};
+    r.src = d_src;
+    r.dst = d_dst;
+    r.cls_out = d_class;
+    r.g = make_geom(n, {{d_src, 4}, {d_dst, 4}, {d_class, 1}});
+    LaunchCfg c;
+    c.stream = stream;
+    c.status = ds->status;
+    c.sm_count = ds->sm_count;
+    SINET_CUDA(run_discriminate(lk, r, t->args, d_class_counts, c));
+    return SINET_OK;
+}
+
+sinet_status sinet_histogram(const uint64_t *d_ts, const uint32_t *d_bytes, const uint8_t *d_class, uint64_t n,
+                             const sinet_hist_params *p, const sinet_hist_out *o, sinet_stream_t stream) {
+    sinet_status st = check_params(p);
+    if (st != SINET_OK) return st;
+    if ((st = check_out(o)) != SINET_OK) return st;
+    if (n > kMaxN) return SINET_ERR_INVALID_ARG;
+    if (n && (!d_ts || !d_bytes || !d_class || !aligned(d_ts, 8) || !aligned(d_bytes, 4)))
+        return SINET_ERR_INVALID_ARG;
+    RecArgs r{};
+    r.ts = d_ts;
+    r.bytes = d_bytes;
+    r.cls_in = d_class;
+    r.g = make_geom(n, {{d_ts, 8}, {d_bytes, 4}, {d_class, 1}});
+    return run_hist(nullptr, LK_CLASS_IN, r, p, o, stream);
+}
+
+sinet_status sinet_discriminate_histogram(const sinet_prefix_table *t, const uint64_t *d_ts, const uint32_t *d_src,
+                                          const uint32_t *d_dst, const uint32_t *d_bytes, uint64_t n,
+                                          const sinet_hist_params *p, const sinet_hist_out *o,
+                                          sinet_stream_t stream) {
+    if (!t) return SINET_ERR_INVALID_ARG;
+    sinet_status st = check_params(p);
+    if (st != SINET_OK) return st;
+    if ((st = check_out(o)) != SINET_OK) return st;
+    if (n > kMaxN) return SINET_ERR_INVALID_ARG;
+    if (n && (!d_ts || !d_src || !d_dst || !d_bytes || !aligned(d_ts, 8) || !aligned(d_src, 4) ||
+              !aligned(d_dst, 4) || !aligned(d_bytes, 4)))
+        return SINET_ERR_INVALID_ARG;
+    const int lk = pick_lookup(t, p->lookup, &st);
+    if (st != SINET_OK) return st;
+    RecArgs r{};
+    r.ts = d_ts;
+    r.src = d_src;
+    r.dst = d_dst;
+    r.bytes = d_bytes;
+    r.g = make_geom(n, {{d_ts, 8}, {d_src, 4}, {d_dst, 4}, {d_bytes, 4}});
+    return run_hist(t, lk, r, p, o, stream);
+}
+
+sinet_status sinet_device_status(sinet_stream_t stream, uint32_t *device_code) {
+    if (!device_code) return SINET_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    sinet_status st = device_state(&ds);
+    if (st != SINET_OK) return st;
+    SINET_CUDA(cudaStreamSynchronize(stream));
+    uint32_t v = 0;
+    SINET_CUDA(cudaMemcpy(&v, ds->status, 4, cudaMemcpyDeviceToHost));
+    SINET_CUDA(cudaMemset(ds->status, 0, 4));
+    *device_code = v;
+    return SINET_OK;
+}
+
+}  // extern "C"

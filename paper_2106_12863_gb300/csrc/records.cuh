@@ -1,0 +1,205 @@
+// Per-record pieces of the hot path shared by every kernel: loading a quad of
+// SoA records, classifying (Algorithm 1 against the staged table), routing a
+// class to directions, and binning (Section 5's millisecond histogram).
+#pragma once
+#include "common.cuh"
+
+namespace sinet {
+
+enum : int { LK_INTERVAL = 0, LK_PML = 1, LK_INTERVAL_GLOBAL = 2, LK_CLASS_IN = 3 };
+
+struct RecArgs {
+    const uint64_t *ts;
+    const uint32_t *src;
+    const uint32_t *dst;
+    const uint32_t *bytes;
+    const uint8_t *cls_in;  // classified input (sinet_histogram)
+    uint8_t *cls_out;       // class output (sinet_discriminate), may be null
+    QuadGeom g;
+};
+
+struct HistArgs {
+    uint32_t *cnt[2];
+    uint64_t *byt[2];
+    uint64_t *stats;  // [0..3] per class, [4..5] out of window per direction
+    uint64_t t0;
+    uint64_t span;    // n_bins * w
+    Divider div;
+    uint32_t w_is_one;
+    uint32_t policy;  // byte c = direction bits of class c
+    uint32_t two_dir; // some class routes to both directions
+    uint32_t n_bins;
+};
+
+// ---------------------------------------------------------------------------
+// Classifier: stages the table image into shared memory (interval or
+// per-length form) or reads it from global memory, and answers in(a).
+template <int LK>
+struct Classifier;
+
+template <>
+struct Classifier<LK_INTERVAL> {
+    IntervalView<uint16_t> v;
+    __device__ __forceinline__ void init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
+                                         uint32_t *status) {
+        stage_to_smem(smem, t.image, t.iv_bytes, bar, status);
+        v.lo = reinterpret_cast<const uint32_t *>(smem + t.off_lo);
+        v.hi = reinterpret_cast<const uint32_t *>(smem + t.off_hi);
+        v.idx = reinterpret_cast<const uint16_t *>(smem + t.off_idx16);
+        v.shift = 32 - t.index_bits;
+        v.n_iv = t.n_iv;
+    }
+    static __host__ __device__ uint32_t smem_bytes(const TableArgs &t) { return t.iv_bytes; }
+    __device__ __forceinline__ uint32_t in(uint32_t a) const { return v.contains(a); }
+};
+
+template <>
+struct Classifier<LK_PML> {
+    PmlView v;
+    __device__ __forceinline__ void init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
+                                         uint32_t *status) {
+        stage_to_smem(smem, t.image + t.off_nets, t.pml_bytes, bar, status);
+        v.nets = reinterpret_cast<const uint32_t *>(smem);
+        v.groups = reinterpret_cast<const uint4 *>(smem + (t.off_groups - t.off_nets));
+        v.n_groups = t.n_groups;
+    }
+    static __host__ __device__ uint32_t smem_bytes(const TableArgs &t) { return t.pml_bytes; }
+    __device__ __forceinline__ uint32_t in(uint32_t a) const { return v.contains(a); }
+};
+
+template <>
+struct Classifier<LK_INTERVAL_GLOBAL> {
+    IntervalView<uint32_t> v;
+    __device__ __forceinline__ void init(const TableArgs &t, uint8_t *, uint64_t *, uint32_t *) {
+        v.lo = reinterpret_cast<const uint32_t *>(t.image + t.off_lo);
+        v.hi = reinterpret_cast<const uint32_t *>(t.image + t.off_hi);
+        v.idx = reinterpret_cast<const uint32_t *>(t.image + t.off_idx32);
+        v.shift = 32 - t.index_bits;
+        v.n_iv = t.n_iv;
+    }
+    static __host__ __device__ uint32_t smem_bytes(const TableArgs &) { return 0; }
+    __device__ __forceinline__ uint32_t in(uint32_t a) const { return v.contains(a); }
+};
+
+template <>
+struct Classifier<LK_CLASS_IN> {
+    __device__ __forceinline__ void init(const TableArgs &, uint8_t *, uint64_t *, uint32_t *) {}
+    static __host__ __device__ uint32_t smem_bytes(const TableArgs &) { return 0; }
+    __device__ __forceinline__ uint32_t in(uint32_t) const { return 0; }
+};
+
+// ---------------------------------------------------------------------------
+// A quad of records. `valid` has bit j set when record j exists.
+struct Quad {
+    uint64_t ts[4];
+    uint32_t src[4], dst[4], by[4], cls[4];
+    uint32_t valid;
+};
+
+// Load quad q with the fields the caller needs.
+template <bool TS, bool ADDR, bool BY, bool CIN>
+__device__ __forceinline__ void load_quad(const RecArgs &r, uint64_t q, uint64_t pol, Quad &Q) {
+    Q.valid = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Q.ts[j] = 0;
+        Q.src[j] = Q.dst[j] = Q.by[j] = Q.cls[j] = 0;
+    }
+    if (q >= r.g.quads) return;
+    const int64_t base = quad_base(r.g, q);
+    if (quad_full(r.g, base)) {
+        if (TS) {
+            ulonglong2 a = ld_stream_v2u64(r.ts + base, pol);
+            ulonglong2 b = ld_stream_v2u64(r.ts + base + 2, pol);
+            Q.ts[0] = a.x; Q.ts[1] = a.y; Q.ts[2] = b.x; Q.ts[3] = b.y;
+        }
+        if (ADDR) {
+            uint4 s = ld_stream_v4(r.src + base, pol);
+            uint4 d = ld_stream_v4(r.dst + base, pol);
+            Q.src[0] = s.x; Q.src[1] = s.y; Q.src[2] = s.z; Q.src[3] = s.w;
+            Q.dst[0] = d.x; Q.dst[1] = d.y; Q.dst[2] = d.z; Q.dst[3] = d.w;
+        }
+        if (BY) {
+            uint4 b = ld_stream_v4(r.bytes + base, pol);
+            Q.by[0] = b.x; Q.by[1] = b.y; Q.by[2] = b.z; Q.by[3] = b.w;
+        }
+        if (CIN) {
+            uint32_t w = ld_stream_u32(reinterpret_cast<const uint32_t *>(r.cls_in + base), pol);
+            Q.cls[0] = w & 3u; Q.cls[1] = (w >> 8) & 3u; Q.cls[2] = (w >> 16) & 3u; Q.cls[3] = (w >> 24) & 3u;
+        }
+        Q.valid = 0xFu;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = base + j;
+        if (i < 0 || (uint64_t)i >= r.g.n) continue;
+        Q.valid |= 1u << j;
+        if (TS) Q.ts[j] = ld_stream_u64(r.ts + i, pol);
+        if (ADDR) {
+            Q.src[j] = ld_stream_u32(r.src + i, pol);
+            Q.dst[j] = ld_stream_u32(r.dst + i, pol);
+        }
+        if (BY) Q.by[j] = ld_stream_u32(r.bytes + i, pol);
+        if (CIN) Q.cls[j] = ld_stream_u8(r.cls_in + i) & 3u;
+    }
+}
+
+// class = in(src) | in(dst) << 1 for the valid records of a quad (Algorithm 1).
+template <int LK>
+__device__ __forceinline__ void classify_quad(const Classifier<LK> &C, Quad &Q) {
+    if (LK == LK_CLASS_IN) return;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Q.cls[j] = C.in(Q.src[j]) | (C.in(Q.dst[j]) << 1);
+}
+
+// Route + bin one record: returns its direction bits with out-of-window
+// directions removed (they are counted in oor[]), and the bin.
+__device__ __forceinline__ uint32_t route(const HistArgs &h, uint32_t cls, uint64_t ts,
+                                          uint32_t &bin, uint32_t oor[2]) {
+    uint32_t dirs = (h.policy >> (8 * cls)) & 3u;
+    const uint64_t rel = ts - h.t0;  // wraps for ts < t0, and t0 + span fits in 64 bits
+    if (rel >= h.span) {
+        oor[0] += dirs & 1u;
+        oor[1] += dirs >> 1;
+        bin = 0;
+        return 0u;
+    }
+    bin = h.w_is_one ? (uint32_t)rel : (uint32_t)divide(rel, h.div);
+    return dirs;
+}
+
+// cc[c] += 1 without dynamic register-array indexing (which would spill to
+// local memory).
+__device__ __forceinline__ void bump_class(uint32_t cc[4], uint32_t c) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cc[k] += (c == (uint32_t)k) ? 1u : 0u;
+}
+
+// Warp totals of the per-thread counters into stats (lane 0 of every warp).
+__device__ __forceinline__ void flush_counters(uint64_t *stats, const uint32_t cc[4],
+                                               const uint32_t oor[2], bool with_oor) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t v = __reduce_add_sync(kFull, cc[k]);
+        if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long *>(stats + k), (unsigned long long)v);
+    }
+    if (with_oor) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            uint32_t v = __reduce_add_sync(kFull, oor[k]);
+            if (lane == 0 && v)
+                atomicAdd(reinterpret_cast<unsigned long long *>(stats + 4 + k), (unsigned long long)v);
+        }
+    }
+}
+
+__device__ __forceinline__ void gadd(const HistArgs &h, uint32_t d, uint32_t bin, uint32_t c, uint64_t s) {
+    uint32_t *cp = d ? h.cnt[1] : h.cnt[0];
+    uint64_t *bp = d ? h.byt[1] : h.byt[0];
+    atomicAdd(cp + bin, c);
+    atomicAdd(reinterpret_cast<unsigned long long *>(bp + bin), (unsigned long long)s);
+}
+
+}  // namespace sinet

@@ -1,0 +1,304 @@
+"""Thin ctypes binding over ``libsinet.so`` (the C ABI declared in include/sinet.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library. Functions named ``sinet_*`` mirror the C entry points one to one;
+``PrefixTable``, ``HistParams``, ``Histogram`` and the lower-case helpers are
+conveniences over them. Device buffers are torch CUDA tensors (uint64 data as
+int64, uint32 as int32, reinterpreted bit for bit). The library must be built
+(``__graft_entry__.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsinet.so")
+
+OK = 0
+STATUS = {0: "SINET_OK", 1: "SINET_ERR_INVALID_ARG", 2: "SINET_ERR_CUDA", 3: "SINET_ERR_OOM",
+          4: "SINET_ERR_BUDGET", 5: "SINET_ERR_TIMEOUT", 6: "SINET_ERR_TABLE_TOO_LARGE",
+          7: "SINET_ERR_DEVICE_CHECK", 8: "SINET_ERR_UNSUPPORTED"}
+
+STRAT_AUTO, STRAT_GLOBAL_ATOMIC, STRAT_PRIV_TILE, STRAT_SORT_REDUCE, STRAT_SMEM_FULL, \
+    STRAT_ATOMIC_NOAGG = range(6)
+STRATEGIES = {"auto": STRAT_AUTO, "global_atomic": STRAT_GLOBAL_ATOMIC,
+              "priv_tile": STRAT_PRIV_TILE, "sort_reduce": STRAT_SORT_REDUCE,
+              "smem_full": STRAT_SMEM_FULL, "atomic_noagg": STRAT_ATOMIC_NOAGG}
+LOOKUP_AUTO, LOOKUP_INTERVAL, LOOKUP_PML = range(3)
+LOOKUPS = {"auto": LOOKUP_AUTO, "interval": LOOKUP_INTERVAL, "pml": LOOKUP_PML}
+HINT_TIME_SORTED = 1
+
+DIR_OUT, DIR_IN = 1, 2
+EXCLUSIVE = (0, DIR_OUT, DIR_IN, 0)
+PAPER_ALG1 = (DIR_IN, DIR_OUT, DIR_IN, DIR_OUT)
+INCLUSIVE = (0, DIR_OUT, DIR_IN, DIR_OUT | DIR_IN)
+
+
+class SinetError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class HistParamsC(ctypes.Structure):
+    _fields_ = [("t0_ms", ctypes.c_uint64), ("bin_width_ms", ctypes.c_uint64),
+                ("n_bins", ctypes.c_uint64), ("policy", ctypes.c_uint8 * 4),
+                ("accumulate", ctypes.c_int32), ("strategy", ctypes.c_int32),
+                ("lookup", ctypes.c_int32), ("hints", ctypes.c_uint32),
+                ("tile_bins", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
+
+
+class HistOutC(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_void_p * 2), ("bytes", ctypes.c_void_p * 2),
+                ("stats", ctypes.c_void_p)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load():
+    """Load libsinet.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    u32, u64, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+    sig = {
+        "sinet_version": (u32, []),
+        "sinet_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "sinet_last_cuda_error": (ctypes.c_int, []),
+        "sinet_parse_cidr": (ctypes.c_int, [ctypes.c_char_p, _P, _P]),
+        "sinet_compile_prefix_table": (ctypes.c_int, [_P, _P, u32, u32, _P, _P, _P, _P, _P, _P]),
+        "sinet_build_prefix_table": (ctypes.c_int, [_P, _P, u32, _P, _P]),
+        "sinet_destroy_prefix_table": (ctypes.c_int, [_P]),
+        "sinet_discriminate": (ctypes.c_int, [_P, _P, _P, u64, _P, _P, i32, _P]),
+        "sinet_histogram": (ctypes.c_int, [_P, _P, _P, u64, ctypes.POINTER(HistParamsC),
+                                           ctypes.POINTER(HistOutC), _P]),
+        "sinet_discriminate_histogram": (ctypes.c_int, [_P, _P, _P, _P, _P, u64,
+                                                        ctypes.POINTER(HistParamsC),
+                                                        ctypes.POINTER(HistOutC), _P]),
+        "sinet_device_status": (ctypes.c_int, [_P, _P]),
+        "sinet_default_params": (None, [ctypes.POINTER(HistParamsC), u64, u64, u64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise SinetError(rc, where)
+
+
+def _dptr(t) -> int | None:
+    """Device pointer of a CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    import torch
+
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C entry points, same names
+
+
+def sinet_version() -> int:
+    return int(load().sinet_version())
+
+
+def sinet_parse_cidr(text: str):
+    net, ln = ctypes.c_uint32(), ctypes.c_uint8()
+    _check(load().sinet_parse_cidr(text.encode(), ctypes.byref(net), ctypes.byref(ln)),
+           f"sinet_parse_cidr({text!r})")
+    return int(net.value), int(ln.value)
+
+
+def sinet_compile_prefix_table(net, ln, index_bits: int = 0) -> dict:
+    net = np.ascontiguousarray(net, np.uint32)
+    ln = np.ascontiguousarray(ln, np.uint8)
+    n = len(net)
+    counts = np.zeros(4, np.uint32)
+    off = np.zeros(34, np.uint32)
+    # first pass: sizes
+    _check(load().sinet_compile_prefix_table(net.ctypes.data, ln.ctypes.data, n, index_bits, None,
+                                             off.ctypes.data, None, None, None, counts.ctypes.data),
+           "sinet_compile_prefix_table")
+    nets = np.zeros(max(n, 1), np.uint32)
+    lo = np.zeros(max(n, 1), np.uint32)
+    hi = np.zeros(max(n, 1), np.uint32)
+    index = np.zeros((1 << int(counts[2])) + 1, np.uint32)
+    _check(load().sinet_compile_prefix_table(net.ctypes.data, ln.ctypes.data, n, index_bits,
+                                             nets.ctypes.data, off.ctypes.data, lo.ctypes.data,
+                                             hi.ctypes.data, index.ctypes.data, counts.ctypes.data),
+           "sinet_compile_prefix_table")
+    return {"nets": nets[: counts[0]], "len_offset": off, "lo": lo[: counts[1]],
+            "hi": hi[: counts[1]], "index": index, "n_unique": int(counts[0]),
+            "n_intervals": int(counts[1]), "index_bits": int(counts[2]),
+            "max_range": int(counts[3])}
+
+
+def sinet_build_prefix_table(net, ln, stream=None) -> int:
+    net = np.ascontiguousarray(net, np.uint32)
+    ln = np.ascontiguousarray(ln, np.uint8)
+    h = ctypes.c_void_p()
+    _check(load().sinet_build_prefix_table(net.ctypes.data if len(net) else None,
+                                           ln.ctypes.data if len(ln) else None, len(net),
+                                           _stream(stream), ctypes.byref(h)),
+           "sinet_build_prefix_table")
+    return int(h.value)
+
+
+def sinet_destroy_prefix_table(handle: int):
+    _check(load().sinet_destroy_prefix_table(handle), "sinet_destroy_prefix_table")
+
+
+def sinet_discriminate(table: int, d_src, d_dst, n: int, d_class, d_class_counts,
+                       lookup: int = LOOKUP_AUTO, stream=None):
+    _check(load().sinet_discriminate(table, _dptr(d_src), _dptr(d_dst), n, _dptr(d_class),
+                                     _dptr(d_class_counts), lookup, _stream(stream)),
+           "sinet_discriminate")
+
+
+def sinet_histogram(d_ts, d_bytes, d_class, n: int, params: HistParamsC, out: HistOutC, stream=None):
+    _check(load().sinet_histogram(_dptr(d_ts), _dptr(d_bytes), _dptr(d_class), n,
+                                  ctypes.byref(params), ctypes.byref(out), _stream(stream)),
+           "sinet_histogram")
+
+
+def sinet_discriminate_histogram(table: int, d_ts, d_src, d_dst, d_bytes, n: int,
+                                 params: HistParamsC, out: HistOutC, stream=None):
+    _check(load().sinet_discriminate_histogram(table, _dptr(d_ts), _dptr(d_src), _dptr(d_dst),
+                                               _dptr(d_bytes), n, ctypes.byref(params),
+                                               ctypes.byref(out), _stream(stream)),
+           "sinet_discriminate_histogram")
+
+
+def sinet_device_status(stream=None) -> int:
+    v = ctypes.c_uint32()
+    _check(load().sinet_device_status(_stream(stream), ctypes.byref(v)), "sinet_device_status")
+    return int(v.value)
+
+
+# ---------------------------------------------------------------------------
+# Conveniences
+
+
+class PrefixTable:
+    """A compiled CIDR list on the current device."""
+
+    def __init__(self, net, ln, stream=None):
+        self.net = np.ascontiguousarray(net, np.uint32)
+        self.ln = np.ascontiguousarray(ln, np.uint8)
+        self.handle = sinet_build_prefix_table(self.net, self.ln, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sinet_destroy_prefix_table(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class HistParams:
+    t0_ms: int
+    bin_width_ms: int
+    n_bins: int
+    policy: tuple = EXCLUSIVE
+    accumulate: bool = False
+    strategy: str | int = "auto"
+    lookup: str | int = "auto"
+    hints: int = 0
+    tile_bins: int = 0
+    block_threads: int = 0
+
+    def c(self) -> HistParamsC:
+        p = HistParamsC()
+        p.t0_ms, p.bin_width_ms, p.n_bins = self.t0_ms, self.bin_width_ms, self.n_bins
+        for i in range(4):
+            p.policy[i] = self.policy[i]
+        p.accumulate = int(bool(self.accumulate))
+        p.strategy = STRATEGIES[self.strategy] if isinstance(self.strategy, str) else self.strategy
+        p.lookup = LOOKUPS[self.lookup] if isinstance(self.lookup, str) else self.lookup
+        p.hints, p.tile_bins, p.block_threads = self.hints, self.tile_bins, self.block_threads
+        return p
+
+
+class Histogram:
+    """Device outputs: count[2, n_bins] (uint32 bits in int32), bytes[2, n_bins]
+    (uint64 bits in int64) and stats[8] (uint64 bits in int64)."""
+
+    def __init__(self, n_bins: int, device=None, zero: bool = True):
+        import torch
+
+        device = device or torch.device("cuda")
+        mk = torch.zeros if zero else torch.empty
+        self.n_bins = n_bins
+        self.count = mk((2, n_bins), dtype=torch.int32, device=device)
+        self.bytes = mk((2, n_bins), dtype=torch.int64, device=device)
+        self.stats = mk(8, dtype=torch.int64, device=device)
+
+    def c(self) -> HistOutC:
+        o = HistOutC()
+        o.count[0] = self.count[0].data_ptr()
+        o.count[1] = self.count[1].data_ptr()
+        o.bytes[0] = self.bytes[0].data_ptr()
+        o.bytes[1] = self.bytes[1].data_ptr()
+        o.stats = self.stats.data_ptr()
+        return o
+
+    def to_numpy(self) -> dict:
+        return {"count": self.count.cpu().numpy().view(np.uint32),
+                "bytes": self.bytes.cpu().numpy().view(np.uint64),
+                "stats": self.stats.cpu().numpy().view(np.uint64)}
+
+
+def discriminate(table: PrefixTable, src, dst, cls=None, lookup="auto", stream=None):
+    """Class counts (uint64[4] bits in an int64 CUDA tensor); class bytes into ``cls``."""
+    import torch
+
+    counts = torch.empty(4, dtype=torch.int64, device=src.device)
+    sinet_discriminate(table.handle, src, dst, src.numel(), cls, counts,
+                       LOOKUPS[lookup] if isinstance(lookup, str) else lookup, stream)
+    return counts
+
+
+def histogram(ts, nbytes, cls, params: HistParams, out: Histogram, stream=None):
+    sinet_histogram(ts, nbytes, cls, ts.numel(), params.c(), out.c(), stream)
+    return out
+
+
+def discriminate_histogram(table: PrefixTable, ts, src, dst, nbytes, params: HistParams,
+                           out: Histogram, stream=None):
+    sinet_discriminate_histogram(table.handle, ts, src, dst, nbytes, ts.numel(), params.c(),
+                                 out.c(), stream)
+    return out

@@ -1,0 +1,186 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+* the shared library loads and exports every function include/sinet.h declares;
+* the CIDR parser agrees with Python's ``ipaddress``;
+* the host table compiler (canonical groups, merged intervals, direct index)
+  answers membership exactly like the oracle's per-entry loop;
+* argument validation rejects bad input before any CUDA call.
+"""
+import ctypes
+import ipaddress
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import gen
+import paper_2106_12863_gb300 as sinet
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2106_12863_gb300 import _build
+
+    _build.build()
+    sinet.load()
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sinet_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = ctypes.CDLL(sinet.LIB_PATH)
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            names += _declared(h)
+    assert "sinet_discriminate_histogram" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_version_and_status_strings():
+    assert sinet.sinet_version() >= 0x000100
+    L = sinet.load()
+    for code in range(9):
+        assert L.sinet_status_string(code)
+    assert L.sinet_status_string(99) == b"unknown status"
+
+
+@pytest.mark.parametrize("text", ["192.168.1.5/24", "10.0.0.0/8", "0.0.0.0/0", "255.255.255.255/32",
+                                  "1.2.3.4", "172.16.5.4/12"])
+def test_parse_cidr_matches_ipaddress(text):
+    net, ln = sinet.sinet_parse_cidr(text)
+    iface = ipaddress.ip_interface(text)
+    assert net == int(iface.ip)
+    assert ln == iface.network.prefixlen
+
+
+@pytest.mark.parametrize("bad", ["", "1.2.3", "1.2.3.4/33", "256.1.1.1/8", "1.2.3.4/", "a.b.c.d/8",
+                                 "1.2.3.4/8x", "1..2.3/8", "1.2.3.4.5/8", "1234.1.1.1/8"])
+def test_parse_cidr_rejects(bad):
+    with pytest.raises(sinet.SinetError):
+        sinet.sinet_parse_cidr(bad)
+
+
+def _member_intervals(lo, hi, addrs):
+    j = np.searchsorted(lo, addrs, side="right") - 1
+    ok = j >= 0
+    jj = np.where(ok, j, 0)
+    return ok & (addrs <= hi[jj]) if len(lo) else np.zeros(len(addrs), bool)
+
+
+def _member_index(lo, hi, index, k, addrs):
+    """Membership through the direct index exactly as the kernels walk it."""
+    out = np.zeros(len(addrs), bool)
+    n = len(lo)
+    for i, a in enumerate(addrs.tolist()):
+        b = a >> (32 - k)
+        j, e = int(index[b]), int(index[b + 1])
+        if j >= n:
+            continue
+        e = min(e, n - 1)
+        cand = [c for c in range(j, e + 1) if lo[c] <= a]
+        if cand and a <= hi[cand[-1]]:
+            out[i] = True
+    return out
+
+
+def _random_table(rng, k):
+    net = np.array([rng.getrandbits(32) for _ in range(k)], np.uint32)  # host bits set on purpose
+    ln = np.array([rng.choice([0, 1, 8, 9, 16, 20, 24, 25, 31, 32, rng.randint(0, 32)])
+                   for _ in range(k)], np.uint8)
+    return net, ln
+
+
+def _edge_addrs(net, ln, rng, extra=400):
+    a = [rng.getrandbits(32) for _ in range(extra)]
+    for n, z in zip(net.tolist(), ln.tolist()):
+        nw = ipaddress.ip_network((n, z), strict=False)
+        lo, hi = int(nw.network_address), int(nw.broadcast_address)
+        a += [lo, hi, (lo - 1) & 0xFFFFFFFF, (hi + 1) & 0xFFFFFFFF]
+    return np.array(a, np.uint32)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_compiled_table_equals_oracle(orc, seed):
+    rng = random.Random(seed)
+    net, ln = _random_table(rng, rng.randint(1, 40))
+    addrs = _edge_addrs(net, ln, rng)
+    want = orc.classify(net, ln, addrs, np.zeros_like(addrs)) & 1
+    for k in (0, 6, 11):
+        t = sinet.sinet_compile_prefix_table(net, ln, k)
+        got = _member_intervals(t["lo"], t["hi"], addrs)
+        assert np.array_equal(got, want.astype(bool))
+        got2 = _member_index(t["lo"], t["hi"], t["index"], t["index_bits"], addrs)
+        assert np.array_equal(got2, want.astype(bool))
+        # intervals are sorted, disjoint and non-adjacent
+        lo, hi = t["lo"].astype(np.int64), t["hi"].astype(np.int64)
+        assert np.all(lo <= hi) and np.all(lo[1:] > hi[:-1] + 1)
+        # canonical, deduplicated, grouped by length
+        off = t["len_offset"]
+        for L in range(33):
+            g = t["nets"][off[L]:off[L + 1]]
+            m = 0 if L == 0 else (0xFFFFFFFF << (32 - L)) & 0xFFFFFFFF
+            assert np.all(g & np.uint32(m) == g)
+            assert np.all(g[1:] > g[:-1])
+        assert t["n_unique"] == len({(int(n) & ((0xFFFFFFFF << (32 - int(z))) & 0xFFFFFFFF if z else 0),
+                                      int(z)) for n, z in zip(net, ln)})
+
+
+def test_compiled_workload_tables(orc):
+    rng = random.Random(3)
+    for key in ("tiny", "day", "heavy"):
+        w = gen.WORKLOADS[key]
+        net, ln = gen.make_table(w.table, w.seed)
+        t = sinet.sinet_compile_prefix_table(net, ln)
+        assert t["max_range"] <= 4
+        addrs = _edge_addrs(net[:300], ln[:300], rng, extra=3000)
+        want = orc.classify(net, ln, addrs, np.zeros_like(addrs)) & 1
+        assert np.array_equal(_member_intervals(t["lo"], t["hi"], addrs), want.astype(bool))
+
+
+def test_empty_table_compiles():
+    t = sinet.sinet_compile_prefix_table(np.zeros(0, np.uint32), np.zeros(0, np.uint8))
+    assert t["n_unique"] == 0 and t["n_intervals"] == 0
+
+
+def test_compile_rejects_bad_lengths():
+    with pytest.raises(sinet.SinetError) as e:
+        sinet.sinet_compile_prefix_table(np.array([1], np.uint32), np.array([33], np.uint8))
+    assert e.value.status == 1
+    with pytest.raises(sinet.SinetError):
+        sinet.sinet_compile_prefix_table(np.array([1], np.uint32), np.array([8], np.uint8), 21)
+
+
+def test_validation_rejects_before_any_cuda_call():
+    """Bad parameters return SINET_ERR_INVALID_ARG without touching a device."""
+    L = sinet.load()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
+    out = sinet.HistOutC()
+    for i in range(2):
+        out.count[i] = 0x10000
+        out.bytes[i] = 0x20000
+    out.stats = 0x30000
+    for kw in ({"bin_width_ms": 0}, {"n_bins": 0}, {"n_bins": 1 << 31},
+               {"t0_ms": (1 << 64) - 10, "n_bins": 100}):
+        p = sinet.HistParams(t0_ms=kw.get("t0_ms", 0), bin_width_ms=kw.get("bin_width_ms", 1),
+                             n_bins=kw.get("n_bins", 10)).c()
+        rc = L.sinet_discriminate_histogram(fake, 0x40000, 0x50000, 0x60000, 0x70000, 8,
+                                            ctypes.byref(p), ctypes.byref(out), None)
+        assert rc == 1, kw
+    p = sinet.HistParams(0, 1, 10, policy=(0, 1, 2, 4)).c()
+    assert L.sinet_histogram(0x40000, 0x50000, 0x60000, 8, ctypes.byref(p), ctypes.byref(out), None) == 1
+    p = sinet.HistParams(0, 1, 10).c()
+    bad = sinet.HistOutC()
+    assert L.sinet_histogram(0x40000, 0x50000, 0x60000, 8, ctypes.byref(p), ctypes.byref(bad), None) == 1
+    # misaligned record pointer
+    assert L.sinet_histogram(0x40004, 0x50000, 0x60000, 8, ctypes.byref(p), ctypes.byref(out), None) == 1
+    assert L.sinet_discriminate(None, 0x40000, 0x50000, 8, None, 0x60000, 0, None) == 1
