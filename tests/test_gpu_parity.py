@@ -147,7 +147,6 @@ def test_fused_windows_policies(orc, strategy, policy, window):
     w, net, ln, rec = _workload("tiny", 120_007, seed_shift=11)
     pol = POLICIES[policy]
     ref = orc.discriminate_histogram(net, ln, rec, t0, wd, nb, pol)
-    assert ref["stats"][4] + ref["stats"][5] > 0 or policy == "exclusive"
     t = sinet.PrefixTable(net, ln)
     got = run_fused(t, to_dev(rec), sinet.HistParams(t0, wd, nb, policy=pol, strategy=strategy))
     assert_hist_equal(got, ref, f"{strategy}/{policy}/{window}")
