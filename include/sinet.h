@@ -202,6 +202,38 @@ sinet_status sinet_discriminate_histogram(const sinet_prefix_table *t, const uin
                                           sinet_stream_t stream);
 
 /*
+ * Allocation-free form of sinet_discriminate_histogram. The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory on
+ * the call path (a host application whose own memory manager owns every
+ * device allocation, or a latency-bound loop where an allocator call could
+ * synchronise the device or fail under fragmentation).
+ *
+ * It always runs the plain path (discriminate, radix sort, reduce by key;
+ * p->strategy is ignored) with its scratch in a fixed 32 MiB device array
+ * that is part of the library image: about 16.5 bytes per routed record,
+ * so a little over 2 M records when every class routes to at most one
+ * direction, about half that when a class routes to both. Larger inputs
+ * return SINET_ERR_BUDGET before anything is launched. The call itself makes
+ * no cudaMalloc/cudaFree or other allocating call; the prefix table is an
+ * input and must have been built beforehand (sinet_build_prefix_table does
+ * allocate).
+ *
+ * The first call on a device looks up that device's copy of the array (once,
+ * with the device current); make that first call before any stream capture.
+ * Every call on a device shares the one array, and calls that overlap on the
+ * GPU (different streams, no ordering between them) race on it: order them.
+ * The array keeps the previous call's contents; the call clears what must
+ * start at zero itself. A device-side failure (a bounded wait that ran out)
+ * is latched into the low 32 bits of stats[7] as a sinet_status code.
+ * Other arguments, outputs and errors as in sinet_discriminate_histogram.
+ */
+sinet_status sinet_discriminate_histogram_noalloc(const sinet_prefix_table *t, const uint64_t *d_ts,
+                                                  const uint32_t *d_src, const uint32_t *d_dst,
+                                                  const uint32_t *d_bytes, uint64_t n,
+                                                  const sinet_hist_params *p,
+                                                  const sinet_hist_out *o, sinet_stream_t stream);
+
+/*
  * Read and clear the device status word of the current device, after
  * synchronising `stream`. *device_code receives the latched sinet_status
  * (SINET_OK if nothing failed).

@@ -4,16 +4,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "launch.h"
-#include "table_host.h"
-
-struct sinet_prefix_table {
-    int device;
-    sinet::TableHost host;
-    sinet::TableImage img;
-    uint8_t *d_image;
-    sinet::TableArgs args;
-};
+#include "api_internal.h"
 
 namespace sinet {
 
@@ -60,7 +51,7 @@ static sinet_status device_state(DeviceState **out) {
 }
 
 // Host side of the invariant-integer divider (Granlund & Montgomery 1994).
-static Divider make_divider(uint64_t w) {
+Divider make_divider(uint64_t w) {
     Divider d{};
     uint32_t l = 0;
     while (l < 64 && (((unsigned __int128)1) << l) < w) l++;
@@ -73,11 +64,7 @@ static Divider make_divider(uint64_t w) {
 
 // Quad geometry: pick the first record index (<= 0) at which every stream is
 // 16-byte aligned (4-byte for byte streams), or fall back to scalar loads.
-struct Stream {
-    const void *p;
-    uint32_t esize;
-};
-static QuadGeom make_geom(uint64_t n, std::initializer_list<Stream> streams) {
+QuadGeom make_geom(uint64_t n, std::initializer_list<Stream> streams) {
     QuadGeom g{};
     g.n = n;
     g.shift = 0;
@@ -100,11 +87,9 @@ static QuadGeom make_geom(uint64_t n, std::initializer_list<Stream> streams) {
     return g;
 }
 
-static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-static const uint64_t kMaxN = 1ull << 40;
-
-static sinet_status check_params(const sinet_hist_params *p) {
+sinet_status check_params(const sinet_hist_params *p) {
     if (!p) return SINET_ERR_INVALID_ARG;
     if (p->bin_width_ms == 0 || p->n_bins == 0 || p->n_bins > 0x7FFFFFFFull) return SINET_ERR_INVALID_ARG;
     const unsigned __int128 end = (unsigned __int128)p->t0_ms + (unsigned __int128)p->n_bins * p->bin_width_ms;
@@ -117,7 +102,7 @@ static sinet_status check_params(const sinet_hist_params *p) {
     return SINET_OK;
 }
 
-static sinet_status check_out(const sinet_hist_out *o) {
+sinet_status check_out(const sinet_hist_out *o) {
     if (!o || !o->count[0] || !o->count[1] || !o->bytes[0] || !o->bytes[1] || !o->stats)
         return SINET_ERR_INVALID_ARG;
     if (!aligned(o->count[0], 4) || !aligned(o->count[1], 4) || !aligned(o->bytes[0], 8) ||
@@ -126,7 +111,7 @@ static sinet_status check_out(const sinet_hist_out *o) {
     return SINET_OK;
 }
 
-static HistArgs make_hist(const sinet_hist_params *p, const sinet_hist_out *o) {
+HistArgs make_hist(const sinet_hist_params *p, const sinet_hist_out *o) {
     HistArgs h{};
     h.cnt[0] = o->count[0];
     h.cnt[1] = o->count[1];
@@ -147,7 +132,7 @@ static HistArgs make_hist(const sinet_hist_params *p, const sinet_hist_out *o) {
     return h;
 }
 
-static sinet_status zero_outputs(const sinet_hist_params *p, const sinet_hist_out *o, cudaStream_t s) {
+sinet_status zero_outputs(const sinet_hist_params *p, const sinet_hist_out *o, cudaStream_t s) {
     if (p->accumulate) return SINET_OK;
     SINET_CUDA(cudaMemsetAsync(o->count[0], 0, 4 * p->n_bins, s));
     SINET_CUDA(cudaMemsetAsync(o->count[1], 0, 4 * p->n_bins, s));
@@ -159,7 +144,7 @@ static sinet_status zero_outputs(const sinet_hist_params *p, const sinet_hist_ou
 
 // Lookup form for a table: the staged interval form when it fits shared
 // memory, the per-length form on request, else global-memory intervals.
-static int pick_lookup(const sinet_prefix_table *t, int32_t lookup, sinet_status *err) {
+int pick_lookup(const sinet_prefix_table *t, int32_t lookup, sinet_status *err) {
     *err = SINET_OK;
     if (lookup == SINET_LOOKUP_PML) {
         if (!t->img.pml_fits_smem) *err = SINET_ERR_UNSUPPORTED;

@@ -84,6 +84,9 @@ def load():
         "sinet_discriminate_histogram": (ctypes.c_int, [_P, _P, _P, _P, _P, u64,
                                                         ctypes.POINTER(HistParamsC),
                                                         ctypes.POINTER(HistOutC), _P]),
+        "sinet_discriminate_histogram_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, u64,
+                                                                ctypes.POINTER(HistParamsC),
+                                                                ctypes.POINTER(HistOutC), _P]),
         "sinet_device_status": (ctypes.c_int, [_P, _P]),
         "sinet_default_params": (None, [ctypes.POINTER(HistParamsC), u64, u64, u64]),
     }
@@ -196,6 +199,15 @@ def sinet_discriminate_histogram(table: int, d_ts, d_src, d_dst, d_bytes, n: int
                                                _dptr(d_bytes), n, ctypes.byref(params),
                                                ctypes.byref(out), _stream(stream)),
            "sinet_discriminate_histogram")
+
+
+def sinet_discriminate_histogram_noalloc(table: int, d_ts, d_src, d_dst, d_bytes, n: int,
+                                         params: HistParamsC, out: HistOutC, stream=None):
+    """The allocation-free plain path (fixed device scratch; see include/sinet.h)."""
+    _check(load().sinet_discriminate_histogram_noalloc(table, _dptr(d_ts), _dptr(d_src), _dptr(d_dst),
+                                                       _dptr(d_bytes), n, ctypes.byref(params),
+                                                       ctypes.byref(out), _stream(stream)),
+           "sinet_discriminate_histogram_noalloc")
 
 
 def sinet_device_status(stream=None) -> int:
