@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="day", choices=sorted(gen.WORKLOADS))
     ap.add_argument("--records", type=int, default=0, help="override the record count")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink records, window and bins together (keeps records per bin; "
+                         "for profiling captures)")
     ap.add_argument("--strategy", default="tune",
                     help="tune | global_atomic | priv_tile | atomic_noagg | sort_reduce")
     ap.add_argument("--plain-steps", type=int, default=20)
@@ -66,9 +69,19 @@ def dist_env():
 
 
 def workload(args, rank):
+    from dataclasses import replace
+
     w = gen.WORKLOADS[args.workload]
     if args.records:
         w = gen.scaled(w, args.records)
+    if args.scale != 1.0:
+        f = args.scale
+        r = w.records
+        span = int((r.t_hi - r.t_lo) * f)
+        rec = replace(r, n=int(r.n * f), t_hi=r.t_lo + span,
+                      zipf_bins=max(1, int(r.zipf_bins * f)))
+        w = replace(w, records=rec, n_bins=max(1, int(w.n_bins * f)),
+                    name=f"{w.name}-scale{f:g}")
     return w
 
 

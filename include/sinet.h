@@ -139,7 +139,8 @@ sinet_status sinet_parse_cidr(const char *text, uint32_t *net, uint8_t *len);
  * that can hold an address of bucket b is among index[b] .. index[b + 1].
  *
  *   h_net, h_len  host arrays of n entries (len <= 32)
- *   index_bits    0..20 (0 = choose: as many bits as fit a shared-memory budget)
+ *   index_bits    0..20 (0 = choose: the fewest bits, >= 6, whose buckets hold
+ *                 at most four candidate intervals, within a shared-memory budget)
  *   nets_by_len   out, capacity n: canonical unique networks, ascending length,
  *                 sorted within each length (may be NULL)
  *   len_offset    out, uint32[34]: length L occupies [len_offset[L], len_offset[L+1])
@@ -154,6 +155,20 @@ sinet_status sinet_compile_prefix_table(const uint32_t *h_net, const uint8_t *h_
                                         uint32_t index_bits, uint32_t *nets_by_len,
                                         uint32_t *len_offset, uint32_t *iv_lo, uint32_t *iv_hi,
                                         uint32_t *index, uint32_t *counts);
+
+/*
+ * The device image of a compiled CIDR list, serialised on the host (no CUDA
+ * call), for inspection and tests. layout (uint32[16]) receives: toggle
+ * blocks offset, bucket descriptor offset, descriptor bits, bytes staged for
+ * the toggle form, per-length networks offset, group table offset, groups,
+ * bytes staged for the per-length form, global lo/hi/index offsets, index
+ * bits, intervals, most toggle blocks of one bucket, and whether each form
+ * fits shared memory. *bytes receives the image size; image (capacity bytes,
+ * may be NULL to query the size) receives the image.
+ */
+sinet_status sinet_prefix_table_image(const uint32_t *h_net, const uint8_t *h_len, uint32_t n,
+                                      uint8_t *image, size_t capacity, uint32_t *layout,
+                                      size_t *bytes);
 
 /*
  * Compile a CIDR list (as sinet_compile_prefix_table) and upload it to the

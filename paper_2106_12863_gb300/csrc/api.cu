@@ -98,7 +98,7 @@ sinet_status check_params(const sinet_hist_params *p) {
         if (p->policy[c] > 3) return SINET_ERR_INVALID_ARG;
     if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_ATOMIC_NOAGG) return SINET_ERR_INVALID_ARG;
     if (p->lookup < SINET_LOOKUP_AUTO || p->lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
-    if (p->block_threads && (p->block_threads > 256 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
+    if (p->block_threads && (p->block_threads > 1024 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
     return SINET_OK;
 }
 
@@ -160,13 +160,17 @@ static uint32_t table_smem(const sinet_prefix_table *t, int lk) {
     return 0;
 }
 
-// Shared-memory budget left for a bin tile after the staged table (and the
-// kernel's static shared memory).
+// Hot-key cache of the warp-aggregated atomic kernel: 2^9 sets x 4 ways
+// (32 KB of shared memory per CTA).
+static const uint32_t kCacheSetBits = 9;
+
+// Bins per direction that fit a shared-memory tile (8 bytes per bin and
+// direction) after the staged table and the kernel's static shared memory.
 static uint32_t tile_capacity(const DeviceState *ds, uint32_t tsm) {
     const size_t reserve = 1024;
     const size_t used = ((tsm + 15u) & ~15u) + reserve;
     if (ds->smem_optin <= used) return 0;
-    return (uint32_t)((ds->smem_optin - used) / 24);
+    return (uint32_t)((ds->smem_optin - used) / 16);
 }
 
 // The histogram step for every strategy (records already validated).
@@ -201,19 +205,24 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     cudaError_t e = cudaSuccess;
     switch (strat) {
         case SINET_STRAT_GLOBAL_ATOMIC:
-            e = run_fused_atomic(lk, true, r, ta_tab, h, c);
+            e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c);
             break;
         case SINET_STRAT_ATOMIC_NOAGG:
-            e = run_fused_atomic(lk, false, r, ta_tab, h, c);
+            e = run_fused_atomic(lk, false, r, ta_tab, h, 0, c);
             break;
         case SINET_STRAT_PRIV_TILE:
         case SINET_STRAT_SMEM_FULL: {
             TileArgs ta{};
+            LaunchCfg ct = c;
+            ct.block = p->block_threads ? (int)p->block_threads : 512;
+            // chunks of at most 8,192 records keep a bin's count within the
+            // 14 bits of a packed tile entry
+            ta.iters = (uint32_t)(2048 / ct.block);
+            if (ta.iters == 0) ta.iters = 1;
             if (strat == SINET_STRAT_SMEM_FULL) {
                 if (p->n_bins > cap) return SINET_ERR_UNSUPPORTED;
                 ta.tile_bins = (uint32_t)p->n_bins;
                 ta.full = 1;
-                ta.iters = 16;
                 ta.margin = 0;
             } else {
                 uint32_t T = p->tile_bins ? p->tile_bins : 4096;
@@ -221,10 +230,9 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
                 if (T == 0) return SINET_ERR_UNSUPPORTED;
                 ta.tile_bins = T;
                 ta.full = 0;
-                ta.iters = 8;
-                ta.margin = T / 8;
+                ta.margin = T / 6;
             }
-            e = run_fused_tile(lk, r, ta_tab, h, ta, c);
+            e = run_fused_tile(lk, r, ta_tab, h, ta, ct);
             break;
         }
         case SINET_STRAT_SORT_REDUCE: {
@@ -344,9 +352,11 @@ sinet_status sinet_build_prefix_table(const uint32_t *h_net, const uint8_t *h_le
     TableArgs &a = t->args;
     a.image = t->d_image;
     a.iv_bytes = t->img.iv_bytes;
+    a.off_blocks = t->img.off_blocks;
+    a.off_desc = t->img.off_desc;
+    a.desc_bits = t->host.desc_bits;
     a.off_lo = t->img.off_lo;
     a.off_hi = t->img.off_hi;
-    a.off_idx16 = t->img.off_idx16;
     a.off_idx32 = t->img.off_idx32;
     a.n_iv = (uint32_t)t->host.lo.size();
     a.index_bits = t->host.index_bits;

@@ -196,11 +196,48 @@ struct PmlView {
     }
 };
 
+// Toggle form (shared memory). For the bucket of the top `bits` address bits,
+// desc gives the membership of the bucket's first address (bit 31) and the
+// blocks (bits 0-23 first, bits 24-27 count) holding the ascending offsets at
+// which membership flips; an address is inside when the start state XOR the
+// parity of the toggles at or below its offset is 1. Pure buckets use block 0
+// (all 0xFFFFFFFF, above every offset), so the first block load is
+// unconditional and the lookup has no data-dependent branch.
+struct ToggleView {
+    const uint4 *blocks;
+    const uint32_t *desc;
+    uint32_t shift;     // 32 - bits
+    uint32_t off_mask;  // (1 << shift) - 1
+
+    template <int N>
+    __device__ __forceinline__ void contains_n(const uint32_t (&a)[N], uint32_t (&in)[N]) const {
+        uint32_t d[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) d[i] = desc[a[i] >> shift];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const uint32_t off = a[i] & off_mask;
+            const uint4 b = blocks[d[i] & 0xFFFFFFu];
+            in[i] = (d[i] >> 31) ^ (off >= b.x) ^ (off >= b.y) ^ (off >= b.z) ^ (off >= b.w);
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const uint32_t nb = (d[i] >> 24) & 0xFu;
+            const uint32_t off = a[i] & off_mask;
+            for (uint32_t k = 1; k < nb; ++k) {
+                const uint4 b = blocks[(d[i] & 0xFFFFFFu) + k];
+                in[i] ^= (off >= b.x) ^ (off >= b.y) ^ (off >= b.z) ^ (off >= b.w);
+            }
+        }
+    }
+};
+
 // Device description of a staged table (byte offsets inside the image).
 struct TableArgs {
     const uint8_t *image;     // device image base
-    uint32_t iv_bytes;        // [lo | hi | idx16] prefix staged for the interval form
-    uint32_t off_lo, off_hi, off_idx16, off_idx32;
+    uint32_t iv_bytes;        // [blocks | desc] staged for the toggle form
+    uint32_t off_blocks, off_desc, desc_bits;
+    uint32_t off_lo, off_hi, off_idx32;  // global-memory interval form
     uint32_t n_iv, index_bits;
     uint32_t off_nets, off_groups, pml_bytes, n_groups;
 };

@@ -43,16 +43,56 @@ __global__ void __launch_bounds__(256) k_discriminate(RecArgs r, TableArgs t, ui
 }
 
 // ---------------------------------------------------------------------------
+// Per-CTA cache of hot (bin, direction) keys in shared memory: 4-way set
+// associative, a key claims an empty way the first time it is seen and keeps
+// it for the rest of the kernel (skewed input puts its hottest keys in first);
+// a key that finds its set full goes to global atomics. Flushed once per CTA.
+struct HotCache {
+    uint32_t *keys;  // [ways * sets], kNoKey when empty
+    uint32_t *cnt;
+    uint32_t *lo;    // byte sums: low words
+    uint32_t *hi;    // byte sums: high words
+    uint32_t set_bits;
+
+    static constexpr uint32_t kWays = 4;
+    static constexpr uint32_t kSlotBytes = 16;
+
+    __device__ __forceinline__ bool add(uint32_t key, uint32_t c, uint64_t s) {
+        const uint32_t set = (key * 0x9E3779B1u) >> (32 - set_bits);
+        uint32_t *kp = keys + kWays * set;
+        uint4 k4;
+        asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(k4.x), "=r"(k4.y), "=r"(k4.z), "=r"(k4.w)
+                     : "r"(smem_u32(kp)));
+        int way = k4.x == key ? 0 : k4.y == key ? 1 : k4.z == key ? 2 : k4.w == key ? 3 : -1;
+        if (way < 0) {
+            const uint32_t cur[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if (way < 0 && cur[w] == kNoKey) {
+                    const uint32_t old = atomicCAS(kp + w, kNoKey, key);
+                    if (old == kNoKey || old == key) way = w;
+                }
+            }
+            if (way < 0) {  // a racing claim may have taken another way for this key
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (way < 0 && *reinterpret_cast<volatile uint32_t *>(kp + w) == key) way = w;
+            }
+        }
+        if (way < 0) return false;
+        const uint32_t i = kWays * set + way;
+        atomicAdd(cnt + i, c);
+        smem_add_wide(lo + i, hi + i, s, 0u);
+        return true;
+    }
+};
+
 // Warp run-combining: lanes holding the same (bin, direction) key elect a
 // leader that adds the group's count (popc of the peer mask) and byte sum.
 // Byte sums are reduced as two 16-bit halves so 32 values of up to 2^32 - 1
 // cannot overflow the 32-bit warp reduction; they are recombined in 64 bits.
-template <bool AGG>
-__device__ __forceinline__ void update_global(const HistArgs &h, uint32_t key, uint32_t b) {
-    if (!AGG) {
-        if (key != kNoKey) gadd(h, key & 1u, key >> 1, 1u, b);
-        return;
-    }
+__device__ __forceinline__ void update_agg(const HistArgs &h, HotCache &hc, uint32_t key, uint32_t b) {
     const uint32_t peers = __match_any_sync(kFull, key);
     if (key == kNoKey) return;
     const uint32_t c = __popc(peers);
@@ -62,12 +102,44 @@ __device__ __forceinline__ void update_global(const HistArgs &h, uint32_t key, u
         const uint32_t hi = __reduce_add_sync(peers, b >> 16);
         s = (uint64_t)lo + ((uint64_t)hi << 16);
     }
-    if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) gadd(h, key & 1u, key >> 1, c, s);
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) {
+        if (!hc.add(key, c, s)) gadd(h, key & 1u, key >> 1, c, s);
+    }
+}
+
+// Walk a quad's records in order; consecutive records with the same (bin,
+// direction) are merged in registers (time-sorted input repeats bins) and each
+// run goes to `emit(key, count, bytes)` with key = bin << 1 | direction.
+template <typename Emit>
+__device__ __forceinline__ void combine_quad(const HistArgs &h, const Quad &Q, uint32_t cc[4],
+                                             uint32_t oor[2], Emit &&emit) {
+    uint32_t pk = kNoKey, pc = 0;
+    uint64_t ps = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!(Q.valid >> j & 1u)) continue;
+        bump_class(cc, Q.cls[j]);
+        uint32_t bin;
+        const uint32_t dirs = route(h, Q.cls[j], Q.ts[j], bin, oor);
+        if (!dirs) continue;
+        const uint32_t key = bin << 1 | (dirs & 1u ? 0u : 1u);
+        if (key == pk) {
+            pc++;
+            ps += Q.by[j];
+        } else {
+            if (pk != kNoKey) emit(pk, pc, ps);
+            pk = key;
+            pc = 1;
+            ps = Q.by[j];
+        }
+        if (dirs == 3u) emit(bin << 1 | 1u, 1u, (uint64_t)Q.by[j]);
+    }
+    if (pk != kNoKey) emit(pk, pc, ps);
 }
 
 template <int LK, bool AGG>
-__global__ void __launch_bounds__(256) k_fused_atomic(RecArgs r, TableArgs t, HistArgs h,
-                                                      uint32_t *status) {
+__global__ void __launch_bounds__(256, 3) k_fused_atomic(RecArgs r, TableArgs t, HistArgs h,
+                                                         uint32_t cache_set_bits, uint32_t *status) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t bar;
     Classifier<LK> C;
@@ -76,6 +148,34 @@ __global__ void __launch_bounds__(256) k_fused_atomic(RecArgs r, TableArgs t, Hi
     uint32_t cc[4] = {0, 0, 0, 0}, oor[2] = {0, 0};
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (!AGG) {
+        for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < r.g.quads; q += stride) {
+            Quad Q;
+            load_quad<true, LK != LK_CLASS_IN, true, LK == LK_CLASS_IN>(r, q, pol, Q);
+            classify_quad<LK>(C, Q);
+            combine_quad(h, Q, cc, oor, [&](uint32_t key, uint32_t c, uint64_t s) {
+                gadd(h, key & 1u, key >> 1, c, s);
+            });
+        }
+        flush_counters(h.stats, cc, oor, true);
+        return;
+    }
+    // hot-key cache after the staged table
+    uint8_t *cm = smem + ((Classifier<LK>::smem_bytes(t) + 15u) & ~15u);
+    const uint32_t slots = HotCache::kWays << cache_set_bits;
+    HotCache hc;
+    hc.keys = reinterpret_cast<uint32_t *>(cm);
+    hc.cnt = hc.keys + slots;
+    hc.lo = hc.cnt + slots;
+    hc.hi = hc.lo + slots;
+    hc.set_bits = cache_set_bits;
+    for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
+        hc.keys[i] = kNoKey;
+        hc.cnt[i] = 0;
+        hc.lo[i] = 0;
+        hc.hi[i] = 0;
+    }
+    __syncthreads();
     // warp-uniform trip count: every lane reaches the warp-synchronous updates
     for (uint64_t q0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane; q0 < r.g.quads;
          q0 += stride) {
@@ -91,54 +191,69 @@ __global__ void __launch_bounds__(256) k_fused_atomic(RecArgs r, TableArgs t, Hi
                 dirs = route(h, Q.cls[j], Q.ts[j], bin, oor);
             }
             const uint32_t key = dirs ? (bin << 1 | (dirs & 1u ? 0u : 1u)) : kNoKey;
-            update_global<AGG>(h, key, Q.by[j]);
+            update_agg(h, hc, key, Q.by[j]);
             if (h.two_dir) {
                 const bool both = dirs == 3u;
-                if (AGG ? __any_sync(kFull, both) : both)
-                    update_global<AGG>(h, both ? (bin << 1 | 1u) : kNoKey, Q.by[j]);
+                if (__any_sync(kFull, both)) update_agg(h, hc, both ? (bin << 1 | 1u) : kNoKey, Q.by[j]);
             }
         }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
+        const uint32_t c = hc.cnt[i];
+        if (c) gadd(h, hc.keys[i] & 1u, hc.keys[i] >> 1, c, (uint64_t)hc.hi[i] << 32 | hc.lo[i]);
     }
     flush_counters(h.stats, cc, oor, true);
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory privatised bins. A CTA takes chunks of blockDim * iters quads;
-// for each chunk it places a tile of `tile_bins` bins per direction just
-// below the chunk's first record (time-sorted input keeps the chunk inside
-// it), adds in shared memory, and flushes the non-zero bins with global
-// atomics. Records outside the tile go straight to global atomics. With
-// `full`, the tile is the whole histogram and is flushed once at the end.
-template <int LK>
-__global__ void __launch_bounds__(256) k_fused_tile(RecArgs r, TableArgs t, HistArgs h, TileArgs ta,
-                                                    uint32_t *status) {
+// Shared-memory privatised bins. A CTA takes chunks of blockDim * iters quads
+// (at most 8,192 records); for each chunk it places a tile of `tile_bins`
+// bins per direction just below the chunk's first record (time-sorted input
+// keeps the chunk inside it). A tile entry is two 32-bit words updated with
+// native shared atomics: the low 32 bits of the byte sum, and a high word
+// holding the record count in its upper 16 bits and the byte sum's bits
+// 32-47 in its lower 16 (a bin of one chunk holds at most 8,192 records,
+// whose bytes sum below 2^45). The touched part of the tile is flushed with
+// global atomics after the chunk. Records outside the tile go straight to
+// global atomics. With `full`, the tile is the whole histogram (base 0).
+template <int LK, bool W1>
+__global__ void __launch_bounds__(1024) k_fused_tile(RecArgs r, TableArgs t, HistArgs h, TileArgs ta,
+                                                     uint32_t *status) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t bar;
-    __shared__ uint32_t s_base;
+    __shared__ uint32_t s_base, s_lo, s_hi;
+    __shared__ unsigned long long s_cnt[6];
     Classifier<LK> C;
     C.init(t, smem, &bar, status);
     const uint32_t T = ta.tile_bins;
-    uint8_t *tile_mem = smem + ((Classifier<LK>::smem_bytes(t) + 15u) & ~15u);
-    uint64_t *tb = reinterpret_cast<uint64_t *>(tile_mem);            // [2][T] byte sums
-    uint32_t *tc = reinterpret_cast<uint32_t *>(tile_mem + 16ull * T);  // [2][T] counts
+    uint32_t *tlo = reinterpret_cast<uint32_t *>(smem + ((Classifier<LK>::smem_bytes(t) + 15u) & ~15u));
+    uint32_t *thi = tlo + 2 * T;
     for (uint32_t i = threadIdx.x; i < 2 * T; i += blockDim.x) {
-        tb[i] = 0;
-        tc[i] = 0;
+        tlo[i] = 0;
+        thi[i] = 0;
     }
+    if (threadIdx.x == 0) {
+        s_lo = 0xFFFFFFFFu;
+        s_hi = 0;
+    }
+    if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
     const uint64_t pol = policy_evict_first();
-    uint32_t cc[4] = {0, 0, 0, 0}, oor[2] = {0, 0};
+    uint64_t ccp = 0;   // packed per-thread class counts, drained every chunk
+    uint32_t oorp = 0;  // packed per-thread out-of-window counts
     const uint64_t qpc = (uint64_t)blockDim.x * ta.iters;
     const uint64_t n_chunks = (r.g.quads + qpc - 1) / qpc;
-    uint32_t base = 0;
+    const uint32_t lane = threadIdx.x & 31;
     __syncthreads();
 
     for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        uint32_t base = 0;
         if (!ta.full) {
             if (threadIdx.x == 0) {
                 int64_t i0 = quad_base(r.g, ch * qpc);
                 if (i0 < 0) i0 = 0;
                 uint32_t b = 0;
-                uint64_t rel = r.ts[i0] - h.t0;
+                const uint64_t rel = r.ts[i0] - h.t0;
                 if (rel < h.span) {
                     b = h.w_is_one ? (uint32_t)rel : (uint32_t)divide(rel, h.div);
                     b = b > ta.margin ? b - ta.margin : 0u;
@@ -148,88 +263,67 @@ __global__ void __launch_bounds__(256) k_fused_tile(RecArgs r, TableArgs t, Hist
             __syncthreads();
             base = s_base;
         }
+        uint32_t omin = 0xFFFFFFFFu, omax = 0;
         for (uint32_t it = 0; it < ta.iters; ++it) {
             const uint64_t q = ch * qpc + (uint64_t)it * blockDim.x + threadIdx.x;
             Quad Q;
             load_quad<true, LK != LK_CLASS_IN, true, LK == LK_CLASS_IN>(r, q, pol, Q);
+            uint32_t bins[4];
+            const uint32_t inr = bin_quad<W1>(h, Q, bins);
             classify_quad<LK>(C, Q);
-            // combine runs of equal (bin, direction) inside the quad before
-            // touching shared memory (sorted input repeats bins)
-            uint32_t pk = kNoKey, pc = 0;
-            uint64_t ps = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!(Q.valid >> j & 1u)) continue;
-                bump_class(cc, Q.cls[j]);
-                uint32_t bin;
-                const uint32_t dirs = route(h, Q.cls[j], Q.ts[j], bin, oor);
+                bump_class_packed(ccp, Q.cls[j]);
+                const uint32_t bin = bins[j];
+                const uint32_t dirs = dirs_of_packed(h, Q.cls[j], inr >> j & 1u, oorp);
                 if (!dirs) continue;
-                const uint32_t key = bin << 1 | (dirs & 1u ? 0u : 1u);
-                if (key == pk) {
-                    pc++;
-                    ps += Q.by[j];
-                } else {
-                    if (pk != kNoKey) {
-                        const uint32_t pd = pk & 1u, off = (pk >> 1) - base;
-                        if (off < T) {
-                            atomicAdd(tc + pd * T + off, pc);
-                            atomicAdd(reinterpret_cast<unsigned long long *>(tb + pd * T + off),
-                                      (unsigned long long)ps);
-                        } else {
-                            gadd(h, pd, pk >> 1, pc, ps);
-                        }
-                    }
-                    pk = key;
-                    pc = 1;
-                    ps = Q.by[j];
-                }
-                if (dirs == 3u) {
-                    const uint32_t off = bin - base;
-                    if (off < T) {
-                        atomicAdd(tc + T + off, 1u);
-                        atomicAdd(reinterpret_cast<unsigned long long *>(tb + T + off),
-                                  (unsigned long long)Q.by[j]);
-                    } else {
-                        gadd(h, 1u, bin, 1u, Q.by[j]);
-                    }
-                }
-            }
-            if (pk != kNoKey) {
-                const uint32_t pd = pk & 1u, off = (pk >> 1) - base;
+                const uint32_t off = bin - base;
                 if (off < T) {
-                    atomicAdd(tc + pd * T + off, pc);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(tb + pd * T + off),
-                              (unsigned long long)ps);
+                    omin = min(omin, off);
+                    omax = max(omax, off);
+                    const uint32_t e = (dirs & 1u) ? off : T + off;
+                    smem_add_wide(tlo + e, thi + e, Q.by[j], 1u << 16);
+                    if (dirs == 3u) smem_add_wide(tlo + T + off, thi + T + off, Q.by[j], 1u << 16);
                 } else {
-                    gadd(h, pd, pk >> 1, pc, ps);
+                    gadd(h, (dirs & 1u) ? 0u : 1u, bin, 1u, Q.by[j]);
+                    if (dirs == 3u) gadd(h, 1u, bin, 1u, Q.by[j]);
                 }
             }
         }
-        if (!ta.full) {
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < 2 * T; i += blockDim.x) {
-                const uint32_t c = tc[i];
-                if (c) {
-                    const uint32_t d = i >= T, off = i - d * T;
-                    gadd(h, d, base + off, c, tb[i]);
-                    tc[i] = 0;
-                    tb[i] = 0;
-                }
-            }
-            __syncthreads();
+        drain_packed(ccp, oorp, s_cnt);
+        // touched range of the tile, then flush it
+        omin = __reduce_min_sync(kFull, omin);
+        omax = __reduce_max_sync(kFull, omax);
+        if (lane == 0 && omin <= omax) {
+            atomicMin(&s_lo, omin);
+            atomicMax(&s_hi, omax);
         }
-    }
-    if (ta.full) {
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < 2 * T; i += blockDim.x) {
-            const uint32_t c = tc[i];
-            if (c) {
-                const uint32_t d = i >= T, off = i - d * T;
-                gadd(h, d, off, c, tb[i]);
+        const uint32_t lo = s_lo, hi = s_hi;
+        if (lo <= hi) {
+            const uint32_t n = hi - lo + 1;
+            for (uint32_t i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+                const uint32_t d = i >= n;
+                const uint32_t off = lo + i - d * n;
+                const uint32_t e = d * T + off;
+                const uint32_t vh = thi[e];
+                if (vh) {
+                    gadd(h, d, base + off, vh >> 16, (uint64_t)(vh & 0xFFFFu) << 32 | tlo[e]);
+                    tlo[e] = 0;
+                    thi[e] = 0;
+                }
             }
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_lo = 0xFFFFFFFFu;
+            s_hi = 0;
+        }
     }
-    flush_counters(h.stats, cc, oor, true);
+    __syncthreads();
+    if (threadIdx.x < 6 && s_cnt[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long *>(h.stats) + threadIdx.x, s_cnt[threadIdx.x]);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,14 +374,15 @@ cudaError_t run_discriminate(int lk, const RecArgs &r, const TableArgs &t, uint6
 }
 
 cudaError_t run_fused_atomic(int lk, bool agg, const RecArgs &r, const TableArgs &t,
-                             const HistArgs &h, const LaunchCfg &c) {
+                             const HistArgs &h, uint32_t cache_set_bits, const LaunchCfg &c) {
     int grid = 0;
     cudaError_t e;
 #define SINET_ATOM(L, A)                                                                        \
     if (lk == L && agg == A) {                                                                  \
-        size_t smem = Classifier<L>::smem_bytes(t);                                             \
+        size_t smem = ((Classifier<L>::smem_bytes(t) + 15u) & ~15u) +                           \
+                      (A ? (size_t)HotCache::kSlotBytes * (HotCache::kWays << cache_set_bits) : 0ull);                 \
         if ((e = launch(k_fused_atomic<L, A>, smem, c, grid)) != cudaSuccess) return e;         \
-        k_fused_atomic<L, A><<<grid, c.block, smem, c.stream>>>(r, t, h, c.status);             \
+        k_fused_atomic<L, A><<<grid, c.block, smem, c.stream>>>(r, t, h, cache_set_bits, c.status); \
         return cudaGetLastError();                                                              \
     }
     SINET_ATOM(LK_INTERVAL, true)
@@ -306,23 +401,24 @@ cudaError_t run_fused_tile(int lk, const RecArgs &r, const TableArgs &t, const H
                            const TileArgs &ta, const LaunchCfg &c) {
     int grid = 0;
     cudaError_t e;
-    switch (lk) {
-#define SINET_TILE(L)                                                                           \
-    case L: {                                                                                   \
-        size_t smem = ((Classifier<L>::smem_bytes(t) + 15u) & ~15u) + 24ull * ta.tile_bins;     \
-        if ((e = launch(k_fused_tile<L>, smem, c, grid)) != cudaSuccess) return e;              \
-        k_fused_tile<L><<<grid, c.block, smem, c.stream>>>(r, t, h, ta, c.status);              \
-        break;                                                                                  \
+    const bool w1 = h.w_is_one != 0;
+#define SINET_TILE(L, W)                                                                        \
+    if (lk == L && w1 == W) {                                                                   \
+        size_t smem = ((Classifier<L>::smem_bytes(t) + 15u) & ~15u) + 16ull * ta.tile_bins;     \
+        if ((e = launch(k_fused_tile<L, W>, smem, c, grid)) != cudaSuccess) return e;           \
+        k_fused_tile<L, W><<<grid, c.block, smem, c.stream>>>(r, t, h, ta, c.status);           \
+        return cudaGetLastError();                                                              \
     }
-        SINET_TILE(LK_INTERVAL)
-        SINET_TILE(LK_PML)
-        SINET_TILE(LK_INTERVAL_GLOBAL)
-        SINET_TILE(LK_CLASS_IN)
+    SINET_TILE(LK_INTERVAL, true)
+    SINET_TILE(LK_INTERVAL, false)
+    SINET_TILE(LK_PML, true)
+    SINET_TILE(LK_PML, false)
+    SINET_TILE(LK_INTERVAL_GLOBAL, true)
+    SINET_TILE(LK_INTERVAL_GLOBAL, false)
+    SINET_TILE(LK_CLASS_IN, true)
+    SINET_TILE(LK_CLASS_IN, false)
 #undef SINET_TILE
-        default:
-            return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace sinet

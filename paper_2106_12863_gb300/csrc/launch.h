@@ -18,7 +18,7 @@ struct TileArgs {
     uint32_t tile_bins;   // bins per direction in the tile (FULL: n_bins)
     uint32_t iters;       // quads per thread per chunk
     uint32_t margin;      // bins kept below a chunk's first record
-    uint32_t full;        // 1: whole histogram privatised, flushed once per CTA
+    uint32_t full;        // 1: the tile is the whole histogram (base 0)
 };
 
 // Algorithm 1 only: class bytes (optional) and class counts.
@@ -26,8 +26,9 @@ cudaError_t run_discriminate(int lk, const RecArgs &r, const TableArgs &t, uint6
                              const LaunchCfg &c);
 
 // Fused discriminate + histogram with global atomics (warp-aggregated or not).
+// `cache_set_bits`: log2 of the sets of the per-CTA hot-key cache (4 ways each).
 cudaError_t run_fused_atomic(int lk, bool agg, const RecArgs &r, const TableArgs &t,
-                             const HistArgs &h, const LaunchCfg &c);
+                             const HistArgs &h, uint32_t cache_set_bits, const LaunchCfg &c);
 
 // Fused discriminate + histogram with shared-memory bin tiles.
 cudaError_t run_fused_tile(int lk, const RecArgs &r, const TableArgs &t, const HistArgs &h,

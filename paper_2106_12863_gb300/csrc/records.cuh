@@ -39,18 +39,20 @@ struct Classifier;
 
 template <>
 struct Classifier<LK_INTERVAL> {
-    IntervalView<uint16_t> v;
+    ToggleView v;
     __device__ __forceinline__ void init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
                                          uint32_t *status) {
         stage_to_smem(smem, t.image, t.iv_bytes, bar, status);
-        v.lo = reinterpret_cast<const uint32_t *>(smem + t.off_lo);
-        v.hi = reinterpret_cast<const uint32_t *>(smem + t.off_hi);
-        v.idx = reinterpret_cast<const uint16_t *>(smem + t.off_idx16);
-        v.shift = 32 - t.index_bits;
-        v.n_iv = t.n_iv;
+        v.blocks = reinterpret_cast<const uint4 *>(smem + t.off_blocks);
+        v.desc = reinterpret_cast<const uint32_t *>(smem + t.off_desc);
+        v.shift = 32 - t.desc_bits;
+        v.off_mask = (1u << v.shift) - 1u;
     }
     static __host__ __device__ uint32_t smem_bytes(const TableArgs &t) { return t.iv_bytes; }
-    __device__ __forceinline__ uint32_t in(uint32_t a) const { return v.contains(a); }
+    template <int N>
+    __device__ __forceinline__ void in_n(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
+        v.contains_n<N>(a, r);
+    }
 };
 
 template <>
@@ -64,7 +66,11 @@ struct Classifier<LK_PML> {
         v.n_groups = t.n_groups;
     }
     static __host__ __device__ uint32_t smem_bytes(const TableArgs &t) { return t.pml_bytes; }
-    __device__ __forceinline__ uint32_t in(uint32_t a) const { return v.contains(a); }
+    template <int N>
+    __device__ __forceinline__ void in_n(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[i] = v.contains(a[i]);
+    }
 };
 
 template <>
@@ -78,14 +84,22 @@ struct Classifier<LK_INTERVAL_GLOBAL> {
         v.n_iv = t.n_iv;
     }
     static __host__ __device__ uint32_t smem_bytes(const TableArgs &) { return 0; }
-    __device__ __forceinline__ uint32_t in(uint32_t a) const { return v.contains(a); }
+    template <int N>
+    __device__ __forceinline__ void in_n(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[i] = v.contains(a[i]);
+    }
 };
 
 template <>
 struct Classifier<LK_CLASS_IN> {
     __device__ __forceinline__ void init(const TableArgs &, uint8_t *, uint64_t *, uint32_t *) {}
     static __host__ __device__ uint32_t smem_bytes(const TableArgs &) { return 0; }
-    __device__ __forceinline__ uint32_t in(uint32_t) const { return 0; }
+    template <int N>
+    __device__ __forceinline__ void in_n(const uint32_t (&)[N], uint32_t (&r)[N]) const {
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[i] = 0;
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -149,14 +163,26 @@ __device__ __forceinline__ void load_quad(const RecArgs &r, uint64_t q, uint64_t
 template <int LK>
 __device__ __forceinline__ void classify_quad(const Classifier<LK> &C, Quad &Q) {
     if (LK == LK_CLASS_IN) return;
+    uint32_t a[4], r[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) Q.cls[j] = C.in(Q.src[j]) | (C.in(Q.dst[j]) << 1);
+    for (int j = 0; j < 4; ++j) a[j] = Q.src[j];
+    C.template in_n<4>(a, r);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Q.cls[j] = r[j];
+        a[j] = Q.dst[j];
+    }
+    C.template in_n<4>(a, r);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Q.cls[j] |= r[j] << 1;
 }
 
 // Route + bin one record: returns its direction bits with out-of-window
-// directions removed (they are counted in oor[]), and the bin.
-__device__ __forceinline__ uint32_t route(const HistArgs &h, uint32_t cls, uint64_t ts,
-                                          uint32_t &bin, uint32_t oor[2]) {
+// directions removed (they are counted in oor[]), and the bin. W1: the bin
+// width is 1 ms (no division); otherwise division by the invariant width.
+template <bool W1>
+__device__ __forceinline__ uint32_t route_w(const HistArgs &h, uint32_t cls, uint64_t ts,
+                                            uint32_t &bin, uint32_t oor[2]) {
     uint32_t dirs = (h.policy >> (8 * cls)) & 3u;
     const uint64_t rel = ts - h.t0;  // wraps for ts < t0, and t0 + span fits in 64 bits
     if (rel >= h.span) {
@@ -165,8 +191,66 @@ __device__ __forceinline__ uint32_t route(const HistArgs &h, uint32_t cls, uint6
         bin = 0;
         return 0u;
     }
-    bin = h.w_is_one ? (uint32_t)rel : (uint32_t)divide(rel, h.div);
+    bin = W1 ? (uint32_t)rel : (uint32_t)divide(rel, h.div);
     return dirs;
+}
+
+__device__ __forceinline__ uint32_t route(const HistArgs &h, uint32_t cls, uint64_t ts,
+                                          uint32_t &bin, uint32_t oor[2]) {
+    return h.w_is_one ? route_w<true>(h, cls, ts, bin, oor) : route_w<false>(h, cls, ts, bin, oor);
+}
+
+// Bin the quad's timestamps first (so the 64-bit timestamps are dead before
+// the table lookups): bin[j] and bit j of the returned mask for in-window
+// records; out-of-window records keep bin 0.
+template <bool W1>
+__device__ __forceinline__ uint32_t bin_quad(const HistArgs &h, const Quad &Q, uint32_t bin[4]) {
+    uint32_t inr = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint64_t rel = Q.ts[j] - h.t0;
+        const bool in = rel < h.span;
+        bin[j] = in ? (W1 ? (uint32_t)rel : (uint32_t)divide(rel, h.div)) : 0u;
+        inr |= (uint32_t)in << j;
+    }
+    return inr;
+}
+
+// Direction bits of a record from its class; a routed record outside the
+// window is counted in oor[] per direction and routes nowhere.
+__device__ __forceinline__ uint32_t dirs_of(const HistArgs &h, uint32_t cls, bool in_window,
+                                            uint32_t oor[2]) {
+    const uint32_t dirs = (h.policy >> (8 * cls)) & 3u;
+    if (!in_window) {
+        oor[0] += dirs & 1u;
+        oor[1] += dirs >> 1;
+        return 0u;
+    }
+    return dirs;
+}
+
+// dirs_of with the out-of-window counts in a packed word (16 bits per direction).
+__device__ __forceinline__ uint32_t dirs_of_packed(const HistArgs &h, uint32_t cls, bool in_window,
+                                                   uint32_t &oorp) {
+    const uint32_t dirs = (h.policy >> (8 * cls)) & 3u;
+    if (!in_window) {
+        oorp += (dirs & 1u) | ((dirs >> 1) << 16);
+        return 0u;
+    }
+    return dirs;
+}
+
+// A 64-bit sum kept in shared memory as two 32-bit words and updated with
+// native 32-bit atomics: the low word takes the low half of the addend, and
+// the carry out of that add (seen in the returned old value) goes to the high
+// word with the addend's high half. `hi_extra` is added to the high word too
+// (callers pack a count into its upper bits).
+__device__ __forceinline__ void smem_add_wide(uint32_t *lo, uint32_t *hi, uint64_t v, uint32_t hi_extra) {
+    const uint32_t vl = (uint32_t)v;
+    const uint32_t old = atomicAdd(lo, vl);
+    const uint32_t carry = (uint32_t)(old + vl < old);
+    const uint32_t add_hi = (uint32_t)(v >> 32) + carry + hi_extra;
+    if (add_hi) atomicAdd(hi, add_hi);
 }
 
 // cc[c] += 1 without dynamic register-array indexing (which would spill to
@@ -174,6 +258,29 @@ __device__ __forceinline__ uint32_t route(const HistArgs &h, uint32_t cls, uint6
 __device__ __forceinline__ void bump_class(uint32_t cc[4], uint32_t c) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) cc[k] += (c == (uint32_t)k) ? 1u : 0u;
+}
+
+// Per-thread class and out-of-window counters packed in 16-bit fields of one
+// 64-bit word (classes in bits 0-63, four fields) and one 32-bit word (two
+// directions); callers drain them into wider counters before 65,536 records.
+__device__ __forceinline__ void bump_class_packed(uint64_t &cc, uint32_t c) { cc += 1ull << (16 * c); }
+
+// Warp totals of packed counters added into per-CTA shared counters
+// (s_cnt[0..3] classes, s_cnt[4..5] out of window).
+__device__ __forceinline__ void drain_packed(uint64_t &cc, uint32_t &oorp, unsigned long long *s_cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t v = __reduce_add_sync(kFull, (uint32_t)(cc >> (16 * k)) & 0xFFFFu);
+        if (lane == 0 && v) atomicAdd(s_cnt + k, (unsigned long long)v);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const uint32_t v = __reduce_add_sync(kFull, (oorp >> (16 * k)) & 0xFFFFu);
+        if (lane == 0 && v) atomicAdd(s_cnt + 4 + k, (unsigned long long)v);
+    }
+    cc = 0;
+    oorp = 0;
 }
 
 // Warp totals of the per-thread counters into stats (lane 0 of every warp).

@@ -112,41 +112,94 @@ int compile_table(const uint32_t *net, const uint8_t *len, uint32_t n, uint32_t 
     }
     t.index_bits = k;
     t.max_range = build_index(k);
+
+    // toggle form: the fewest bits (8..14) whose buckets hold at most 8
+    // toggles (two blocks) and whose image fits the shared-memory budget
+    auto build_toggles = [&](uint32_t kb, bool keep) {
+        const uint32_t nb = 1u << kb;
+        std::vector<uint32_t> desc(nb, 0), blocks(4, 0xFFFFFFFFu);
+        uint32_t maxb = 1, j = 0;
+        std::vector<uint32_t> tog;
+        for (uint32_t b = 0; b < nb; b++) {
+            const uint64_t start = (uint64_t)b << (32 - kb);
+            const uint64_t end = start + (1ull << (32 - kb)) - 1;
+            while (j < n_iv && (uint64_t)t.hi[j] < start) j++;  // first with hi >= start
+            const uint32_t s0 = (j < n_iv && (uint64_t)t.lo[j] <= start) ? 1u : 0u;
+            tog.clear();
+            for (uint32_t e = j; e < n_iv && (uint64_t)t.lo[e] <= end; e++) {
+                if ((uint64_t)t.lo[e] > start) tog.push_back((uint32_t)((uint64_t)t.lo[e] - start));
+                if ((uint64_t)t.hi[e] < end) tog.push_back((uint32_t)((uint64_t)t.hi[e] + 1 - start));
+            }
+            uint32_t nblk = 1, first = 0;
+            if (!tog.empty()) {
+                nblk = (uint32_t)(tog.size() + 3) / 4;
+                first = (uint32_t)blocks.size() / 4;
+                for (uint32_t i = 0; i < nblk * 4; i++) blocks.push_back(i < tog.size() ? tog[i] : 0xFFFFFFFFu);
+            }
+            maxb = std::max(maxb, nblk);
+            if (nblk > 15 || first > 0xFFFFFFu) return std::pair<uint32_t, size_t>(~0u, ~size_t(0));
+            desc[b] = first | (nblk << 24) | (s0 << 31);
+        }
+        const size_t bytes = 4 * blocks.size() + 4 * (size_t)nb;
+        if (keep) {
+            t.desc.swap(desc);
+            t.blocks.swap(blocks);
+            t.desc_bits = kb;
+            t.max_blocks = maxb;
+        }
+        return std::pair<uint32_t, size_t>(maxb, bytes);
+    };
+    uint32_t kb = 0, fallback = 0;
+    size_t fallback_bytes = ~size_t(0);
+    for (uint32_t c = 8; c <= 14 && !kb; c++) {
+        auto r = build_toggles(c, false);
+        if (r.first == ~0u || r.second > kSmemTableBudget) continue;
+        if (r.first <= 2) kb = c;
+        else if (r.second < fallback_bytes) { fallback = c; fallback_bytes = r.second; }
+    }
+    if (!kb) kb = fallback ? fallback : 14;
+    build_toggles(kb, true);
     return SINET_OK;
 }
 
 std::vector<uint8_t> serialise(const TableHost &t, TableImage &img) {
     const uint32_t n_iv = (uint32_t)t.lo.size();
+    const uint32_t n_pairs = n_iv ? n_iv : 1;  // an empty table keeps one empty interval
     const uint32_t nb1 = (1u << t.index_bits) + 1;
     img = TableImage{};
     uint32_t off = 0;
-    img.off_lo = off;
-    off += pad16(4 * n_iv);
-    img.off_hi = off;
-    off += pad16(4 * n_iv);
-    img.off_idx16 = off;
-    if (n_iv <= 65535) off += pad16(2 * nb1);
+    img.off_blocks = off;
+    off += pad16(4 * (uint32_t)t.blocks.size());
+    img.off_desc = off;
+    off += pad16(4 * (uint32_t)t.desc.size());
     img.iv_bytes = off;
-    img.iv_fits_smem = n_iv <= 65535 && img.iv_bytes <= kSmemTableBudget;
+    img.iv_fits_smem = !t.desc.empty() && t.max_blocks <= 15 && img.iv_bytes <= kSmemTableBudget;
     img.off_nets = off;
     off += pad16(4 * (uint32_t)t.nets.size());
     img.off_groups = off;
     off += 16 * (uint32_t)t.groups.size();
     img.pml_bytes = off - img.off_nets;
     img.pml_fits_smem = img.pml_bytes <= kSmemTableBudget;
+    img.off_lo = off;
+    off += pad16(4 * n_pairs);
+    img.off_hi = off;
+    off += pad16(4 * n_pairs);
     img.off_idx32 = off;
     off += pad16(4 * nb1);
     img.total = off;
 
     std::vector<uint8_t> buf(img.total, 0);
+    uint32_t *lo = reinterpret_cast<uint32_t *>(buf.data() + img.off_lo);
+    uint32_t *hi = reinterpret_cast<uint32_t *>(buf.data() + img.off_hi);
     if (n_iv) {
-        std::memcpy(buf.data() + img.off_lo, t.lo.data(), 4 * n_iv);
-        std::memcpy(buf.data() + img.off_hi, t.hi.data(), 4 * n_iv);
+        std::memcpy(lo, t.lo.data(), 4 * n_iv);
+        std::memcpy(hi, t.hi.data(), 4 * n_iv);
+    } else {
+        lo[0] = 1;  // lo > hi: contains nothing
+        hi[0] = 0;
     }
-    if (n_iv <= 65535) {
-        uint16_t *ix = reinterpret_cast<uint16_t *>(buf.data() + img.off_idx16);
-        for (uint32_t b = 0; b < nb1; b++) ix[b] = (uint16_t)t.index[b];
-    }
+    if (!t.blocks.empty()) std::memcpy(buf.data() + img.off_blocks, t.blocks.data(), 4 * t.blocks.size());
+    if (!t.desc.empty()) std::memcpy(buf.data() + img.off_desc, t.desc.data(), 4 * t.desc.size());
     if (!t.nets.empty()) std::memcpy(buf.data() + img.off_nets, t.nets.data(), 4 * t.nets.size());
     uint32_t *g = reinterpret_cast<uint32_t *>(buf.data() + img.off_groups);
     for (size_t i = 0; i < t.groups.size(); i++) {
@@ -179,5 +232,28 @@ extern "C" sinet_status sinet_compile_prefix_table(const uint32_t *h_net, const 
     counts[1] = (uint32_t)t.lo.size();
     counts[2] = t.index_bits;
     counts[3] = t.max_range;
+    return SINET_OK;
+}
+
+extern "C" sinet_status sinet_prefix_table_image(const uint32_t *h_net, const uint8_t *h_len,
+                                                 uint32_t n, uint8_t *image, size_t capacity,
+                                                 uint32_t *layout, size_t *bytes) {
+    if (!layout || !bytes) return SINET_ERR_INVALID_ARG;
+    sinet::TableHost t;
+    int rc = sinet::compile_table(h_net, h_len, n, 0, t);
+    if (rc != SINET_OK) return (sinet_status)rc;
+    sinet::TableImage img;
+    std::vector<uint8_t> buf = sinet::serialise(t, img);
+    *bytes = buf.size();
+    const uint32_t v[16] = {img.off_blocks, img.off_desc, t.desc_bits, img.iv_bytes,
+                            img.off_nets, img.off_groups, (uint32_t)t.groups.size(), img.pml_bytes,
+                            img.off_lo, img.off_hi, img.off_idx32, t.index_bits,
+                            (uint32_t)t.lo.size(), t.max_blocks, img.iv_fits_smem ? 1u : 0u,
+                            img.pml_fits_smem ? 1u : 0u};
+    std::memcpy(layout, v, sizeof v);
+    if (image) {
+        if (capacity < buf.size()) return SINET_ERR_INVALID_ARG;
+        std::memcpy(image, buf.data(), buf.size());
+    }
     return SINET_OK;
 }

@@ -18,6 +18,17 @@ struct TableHost {
     uint32_t index_bits = 0;
     std::vector<uint32_t> index;  // 2^index_bits + 1 entries
     uint32_t max_range = 0;       // largest candidate range of an index bucket
+    // toggle form for shared memory: for each bucket of the top desc_bits
+    // address bits, whether the bucket's first address is inside (bit 31), how
+    // many 4-offset blocks of toggles follow (bits 24-27) and where they start
+    // (bits 0-23). A toggle is the offset from the bucket start at which
+    // membership flips; membership of an address is the start state XOR the
+    // parity of the toggles at or below its offset. Block 0 is all sentinels
+    // (0xFFFFFFFF, never reached) and serves every pure bucket.
+    uint32_t desc_bits = 0;
+    std::vector<uint32_t> desc;
+    std::vector<uint32_t> blocks;  // 4 u32 per block
+    uint32_t max_blocks = 0;       // most blocks one bucket needs
     // per-length groups in probe order (most covered addresses first)
     struct Group { uint32_t len, off, cnt; };
     std::vector<Group> groups;
@@ -30,10 +41,10 @@ int compile_table(const uint32_t *net, const uint8_t *len, uint32_t n, uint32_t 
 
 // Layout of the single contiguous device image (all offsets 16-byte aligned).
 struct TableImage {
-    uint32_t off_lo = 0, off_hi = 0, off_idx16 = 0;  // interval form (u16 index)
-    uint32_t off_nets = 0, off_groups = 0;           // per-length form
-    uint32_t off_idx32 = 0;                          // u32 index for global lookups
-    uint32_t iv_bytes = 0;    // bytes of [lo | hi | idx16] staged for INTERVAL
+    uint32_t off_blocks = 0, off_desc = 0;   // shared-memory toggle form
+    uint32_t off_nets = 0, off_groups = 0;   // per-length form
+    uint32_t off_lo = 0, off_hi = 0, off_idx32 = 0;  // global-memory interval form
+    uint32_t iv_bytes = 0;    // bytes of [blocks | desc] staged for INTERVAL
     uint32_t pml_bytes = 0;   // bytes of [nets | groups] staged for PML
     uint32_t total = 0;
     bool iv_fits_smem = false, pml_fits_smem = false;

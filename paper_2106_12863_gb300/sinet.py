@@ -76,6 +76,7 @@ def load():
         "sinet_last_cuda_error": (ctypes.c_int, []),
         "sinet_parse_cidr": (ctypes.c_int, [ctypes.c_char_p, _P, _P]),
         "sinet_compile_prefix_table": (ctypes.c_int, [_P, _P, u32, u32, _P, _P, _P, _P, _P, _P]),
+        "sinet_prefix_table_image": (ctypes.c_int, [_P, _P, u32, _P, ctypes.c_size_t, _P, _P]),
         "sinet_build_prefix_table": (ctypes.c_int, [_P, _P, u32, _P, _P]),
         "sinet_destroy_prefix_table": (ctypes.c_int, [_P]),
         "sinet_discriminate": (ctypes.c_int, [_P, _P, _P, u64, _P, _P, i32, _P]),
@@ -163,6 +164,26 @@ def sinet_compile_prefix_table(net, ln, index_bits: int = 0) -> dict:
             "hi": hi[: counts[1]], "index": index, "n_unique": int(counts[0]),
             "n_intervals": int(counts[1]), "index_bits": int(counts[2]),
             "max_range": int(counts[3])}
+
+
+LAYOUT_KEYS = ("off_blocks", "off_desc", "desc_bits", "iv_bytes", "off_nets", "off_groups",
+               "n_groups", "pml_bytes", "off_lo", "off_hi", "off_idx32", "index_bits", "n_iv",
+               "max_blocks", "iv_fits_smem", "pml_fits_smem")
+
+
+def sinet_prefix_table_image(net, ln):
+    """(image bytes as numpy uint8, layout dict) of the table's device image."""
+    net = np.ascontiguousarray(net, np.uint32)
+    ln = np.ascontiguousarray(ln, np.uint8)
+    layout = np.zeros(16, np.uint32)
+    size = ctypes.c_size_t()
+    args = (net.ctypes.data if len(net) else None, ln.ctypes.data if len(ln) else None, len(net))
+    _check(load().sinet_prefix_table_image(*args, None, 0, layout.ctypes.data, ctypes.byref(size)),
+           "sinet_prefix_table_image")
+    img = np.zeros(size.value, np.uint8)
+    _check(load().sinet_prefix_table_image(*args, img.ctypes.data, size.value, layout.ctypes.data,
+                                           ctypes.byref(size)), "sinet_prefix_table_image")
+    return img, dict(zip(LAYOUT_KEYS, (int(v) for v in layout)))
 
 
 def sinet_build_prefix_table(net, ln, stream=None) -> int:

@@ -184,3 +184,50 @@ def test_validation_rejects_before_any_cuda_call():
     # misaligned record pointer
     assert L.sinet_histogram(0x40004, 0x50000, 0x60000, 8, ctypes.byref(p), ctypes.byref(out), None) == 1
     assert L.sinet_discriminate(None, 0x40000, 0x50000, 8, None, 0x60000, 0, None) == 1
+
+
+def _toggle_lookup(img, lay, addrs):
+    """The shared-memory toggle lookup of the kernels, replayed on the host."""
+    desc = img[lay["off_desc"]: lay["off_desc"] + 4 * (1 << lay["desc_bits"])].view(np.uint32)
+    blocks = img[lay["off_blocks"]: lay["off_desc"]].view(np.uint32).reshape(-1, 4)
+    shift = 32 - lay["desc_bits"]
+    a = addrs.astype(np.uint64)
+    d = desc[(a >> np.uint64(shift)).astype(np.int64)].astype(np.uint64)
+    off = a & np.uint64((1 << shift) - 1)
+    first = (d & np.uint64(0xFFFFFF)).astype(np.int64)
+    nb = ((d >> np.uint64(24)) & np.uint64(0xF)).astype(np.int64)
+    assert nb.min() >= 1
+    assert (first + nb).max() <= len(blocks)  # every block read stays in the staged region
+    state = (d >> np.uint64(31)).astype(np.uint8)
+    for k in range(int(nb.max())):
+        use = nb > k
+        b = blocks[np.where(use, first + k, 0)].astype(np.uint64)
+        par = ((off[:, None] >= b).sum(axis=1) & 1).astype(np.uint8)
+        state ^= np.where(use, par, 0).astype(np.uint8)
+    return state
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_toggle_form_equals_oracle(orc, seed):
+    rng = random.Random(100 + seed)
+    net, ln = _random_table(rng, rng.randint(0, 60))
+    if seed == 0:
+        net, ln = net[:0], ln[:0]
+    addrs = _edge_addrs(net, ln, rng, extra=3000)
+    img, lay = sinet.sinet_prefix_table_image(net, ln)
+    assert lay["iv_bytes"] % 16 == 0 and lay["off_desc"] % 16 == 0 and lay["iv_bytes"] <= len(img)
+    want = (orc.classify(net, ln, addrs, np.zeros_like(addrs)) & 1) if len(net) else np.zeros(len(addrs), np.uint8)
+    assert np.array_equal(_toggle_lookup(img, lay, addrs), want)
+
+
+def test_toggle_form_on_workload_tables(orc):
+    rng = random.Random(9)
+    for key in ("tiny", "day", "heavy"):
+        w = gen.WORKLOADS[key]
+        net, ln = gen.make_table(w.table, w.seed)
+        img, lay = sinet.sinet_prefix_table_image(net, ln)
+        assert lay["iv_fits_smem"] == 1 and lay["max_blocks"] <= 2
+        r = gen.make_records(gen.scaled(w, 50_000).records, w.seed, net, ln)
+        addrs = np.concatenate([r["src"], r["dst"], _edge_addrs(net[:200], ln[:200], rng, 2000)])
+        want = orc.classify(net, ln, addrs, np.zeros_like(addrs)) & 1
+        assert np.array_equal(_toggle_lookup(img, lay, addrs), want)
