@@ -96,7 +96,7 @@ sinet_status check_params(const sinet_hist_params *p) {
     if (end > (unsigned __int128)UINT64_MAX) return SINET_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (p->policy[c] > 3) return SINET_ERR_INVALID_ARG;
-    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_ATOMIC_NOAGG) return SINET_ERR_INVALID_ARG;
+    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_OWNER) return SINET_ERR_INVALID_ARG;
     if (p->lookup < SINET_LOOKUP_AUTO || p->lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
     if (p->block_threads && (p->block_threads > 1024 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
     return SINET_OK;
@@ -195,12 +195,17 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         if (2ull * p->n_bins <= 8192 && p->n_bins <= cap)
             strat = SINET_STRAT_SMEM_FULL;
         else if (p->hints & SINET_HINT_TIME_SORTED)
-            strat = SINET_STRAT_PRIV_TILE;
+            strat = SINET_STRAT_OWNER;
         else
             strat = SINET_STRAT_GLOBAL_ATOMIC;
     }
-    st = zero_outputs(p, o, s);
-    if (st != SINET_OK) return st;
+    if (strat == SINET_STRAT_OWNER && r.g.n > 0 && !p->accumulate) {
+        // the kernel stores every bin itself; only the counters start at zero
+        SINET_CUDA(cudaMemsetAsync(o->stats, 0, 64, s));
+    } else {
+        st = zero_outputs(p, o, s);
+        if (st != SINET_OK) return st;
+    }
     if (r.g.n == 0) return SINET_OK;
     cudaError_t e = cudaSuccess;
     switch (strat) {
@@ -233,6 +238,33 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
                 ta.margin = T / 6;
             }
             e = run_fused_tile(lk, r, ta_tab, h, ta, ct);
+            break;
+        }
+        case SINET_STRAT_OWNER: {
+            OwnerArgs oa{};
+            LaunchCfg co = c;
+            co.block = p->block_threads ? (int)p->block_threads : 512;
+            oa.iters = (uint32_t)(2048 / co.block);
+            if (oa.iters == 0) oa.iters = 1;
+            uint32_t T = p->tile_bins ? p->tile_bins : 4096;
+            if (T > cap) T = cap & ~255u;
+            if (T == 0) return SINET_ERR_UNSUPPORTED;
+            oa.tile_bins = T;
+            oa.margin = T / 6;
+            oa.accumulate = p->accumulate ? 1u : 0u;
+            const uint64_t qpc = (uint64_t)co.block * oa.iters;
+            const uint64_t n_chunks = (r.g.quads + qpc - 1) / qpc;
+            const size_t bytes = 256 + 8 * n_chunks + 4 * n_chunks;
+            void *scratch = nullptr;
+            e = cudaMallocAsync(&scratch, bytes, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            e = cudaMemsetAsync(scratch, 0, bytes, s);
+            oa.ticket = static_cast<uint64_t *>(scratch);
+            oa.words = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(scratch) + 256);
+            oa.done = reinterpret_cast<uint32_t *>(oa.words + n_chunks);
+            if (e == cudaSuccess) e = run_fused_owner(lk, r, ta_tab, h, oa, co);
+            cudaError_t e2 = cudaFreeAsync(scratch, s);
+            if (e == cudaSuccess) e = e2;
             break;
         }
         case SINET_STRAT_SORT_REDUCE: {
