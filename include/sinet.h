@@ -65,9 +65,7 @@ typedef enum {
     SINET_STRAT_PRIV_TILE = 2,     /* shared-memory bin tile per chunk (time-sorted input) */
     SINET_STRAT_SORT_REDUCE = 3,   /* plain path: discriminate, radix sort, reduce by key */
     SINET_STRAT_SMEM_FULL = 4,     /* whole histogram privatised in shared memory (small n_bins) */
-    SINET_STRAT_ATOMIC_NOAGG = 5,  /* global atomics without warp aggregation */
-    SINET_STRAT_OWNER = 6          /* shared-memory tiles; each chunk stores the bins it owns
-                                      once, no zeroing pass (time-sorted input) */
+    SINET_STRAT_ATOMIC_NOAGG = 5   /* global atomics without warp aggregation */
 } sinet_strategy;
 
 /* How membership is looked up. Both are exact. */

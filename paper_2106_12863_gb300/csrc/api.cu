@@ -1,4 +1,5 @@
 // C ABI: argument validation, table upload, strategy dispatch, scratch.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -12,6 +13,7 @@ struct DeviceState {
     bool ready = false;
     int sm_count = 0;
     size_t smem_optin = 0;
+    size_t smem_per_sm = 0;
     uint32_t *status = nullptr;  // device status word
 };
 
@@ -42,6 +44,8 @@ static sinet_status device_state(DeviceState **out) {
         d.sm_count = v;
         SINET_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         d.smem_optin = (size_t)v;
+        SINET_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        d.smem_per_sm = (size_t)v;
         SINET_CUDA(cudaMalloc(&d.status, 256));
         SINET_CUDA(cudaMemset(d.status, 0, 256));
         d.ready = true;
@@ -96,7 +100,7 @@ sinet_status check_params(const sinet_hist_params *p) {
     if (end > (unsigned __int128)UINT64_MAX) return SINET_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (p->policy[c] > 3) return SINET_ERR_INVALID_ARG;
-    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_OWNER) return SINET_ERR_INVALID_ARG;
+    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_ATOMIC_NOAGG) return SINET_ERR_INVALID_ARG;
     if (p->lookup < SINET_LOOKUP_AUTO || p->lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
     if (p->block_threads && (p->block_threads > 1024 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
     return SINET_OK;
@@ -150,12 +154,13 @@ int pick_lookup(const sinet_prefix_table *t, int32_t lookup, sinet_status *err) 
         if (!t->img.pml_fits_smem) *err = SINET_ERR_UNSUPPORTED;
         return LK_PML;
     }
-    return t->img.iv_fits_smem ? LK_INTERVAL : LK_INTERVAL_GLOBAL;
+    if (!t->img.iv_fits_smem) return LK_INTERVAL_GLOBAL;
+    return t->host.toggle_form == 1 ? LK_TOGGLE1 : t->host.toggle_form == 2 ? LK_TOGGLE2 : LK_INTERVAL;
 }
 
 static uint32_t table_smem(const sinet_prefix_table *t, int lk) {
     if (!t) return 0;
-    if (lk == LK_INTERVAL) return t->img.iv_bytes;
+    if (lk == LK_INTERVAL || lk == LK_TOGGLE1 || lk == LK_TOGGLE2) return t->img.iv_bytes;
     if (lk == LK_PML) return t->img.pml_bytes;
     return 0;
 }
@@ -170,7 +175,16 @@ static uint32_t tile_capacity(const DeviceState *ds, uint32_t tsm) {
     const size_t reserve = 1024;
     const size_t used = ((tsm + 15u) & ~15u) + reserve;
     if (ds->smem_optin <= used) return 0;
-    return (uint32_t)((ds->smem_optin - used) / 16);
+    return (uint32_t)((ds->smem_optin - used) / 16) & ~3u;
+}
+
+// Tile bins that still let two CTAs share one SM's shared memory.
+static uint32_t tile_capacity_pair(const DeviceState *ds, uint32_t tsm) {
+    const size_t reserve = 2048;  // static shared memory and per-CTA reservation
+    const size_t per_cta = ds->smem_per_sm / 2;
+    const size_t used = ((tsm + 15u) & ~15u) + reserve;
+    if (per_cta <= used) return 0;
+    return (uint32_t)((per_cta - used) / 16) & ~3u;
 }
 
 // The histogram step for every strategy (records already validated).
@@ -180,6 +194,7 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     sinet_status st = device_state(&ds);
     if (st != SINET_OK) return st;
     HistArgs h = make_hist(p, o);
+    h.status = ds->status;
     TableArgs ta_tab{};
     if (t) ta_tab = t->args;
     LaunchCfg c;
@@ -195,18 +210,45 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         if (2ull * p->n_bins <= 8192 && p->n_bins <= cap)
             strat = SINET_STRAT_SMEM_FULL;
         else if (p->hints & SINET_HINT_TIME_SORTED)
-            strat = SINET_STRAT_OWNER;
+            strat = SINET_STRAT_PRIV_TILE;
         else
             strat = SINET_STRAT_GLOBAL_ATOMIC;
     }
-    if (strat == SINET_STRAT_OWNER && r.g.n > 0 && !p->accumulate) {
-        // the kernel stores every bin itself; only the counters start at zero
-        SINET_CUDA(cudaMemsetAsync(o->stats, 0, 64, s));
-    } else {
-        st = zero_outputs(p, o, s);
-        if (st != SINET_OK) return st;
+
+    // launch shapes first, so an unsupported combination fails before anything is enqueued
+    TileArgs ta{};
+    LaunchCfg ct = c;
+    if (strat == SINET_STRAT_PRIV_TILE || strat == SINET_STRAT_SMEM_FULL) {
+        ct.block = p->block_threads ? (int)p->block_threads : 512;
+        if (strat == SINET_STRAT_SMEM_FULL) {
+            ta.tile_bins = (uint32_t)((p->n_bins + 3) & ~3ull);  // whole histogram
+            if (ta.tile_bins > cap) return SINET_ERR_UNSUPPORTED;
+            ta.full = 1;
+            ta.margin = 0;
+            ta.iters = (uint32_t)(2048 / ct.block);
+        } else {
+            // default: as many bins as let two CTAs share an SM (at most
+            // 4,096), and chunks of about two records per tile bin
+            uint32_t T = p->tile_bins ? p->tile_bins : std::min<uint32_t>(4096, tile_capacity_pair(ds, tsm));
+            if (T > cap) T = cap;
+            T &= ~255u;
+            if (T == 0) return SINET_ERR_UNSUPPORTED;
+            ta.tile_bins = T;
+            ta.full = 0;
+            ta.margin = T / 6;
+            ta.iters = (uint32_t)std::max<uint64_t>(1, (2ull * T) / (4ull * ct.block));
+        }
+        // a chunk stays within 65,535 records: a tile entry counts in 16 bits
+        while ((uint64_t)ct.block * 4 * ta.iters > 65535 && ta.iters > 1) ta.iters--;
+        if (ta.iters == 0) ta.iters = 1;
     }
+    if (strat == SINET_STRAT_SORT_REDUCE && r.g.n * (h.two_dir ? 2ull : 1ull) >= 0xFFFFFFF0ull)
+        return SINET_ERR_UNSUPPORTED;
+
+    st = zero_outputs(p, o, s);
+    if (st != SINET_OK) return st;
     if (r.g.n == 0) return SINET_OK;
+
     cudaError_t e = cudaSuccess;
     switch (strat) {
         case SINET_STRAT_GLOBAL_ATOMIC:
@@ -216,59 +258,10 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
             e = run_fused_atomic(lk, false, r, ta_tab, h, 0, c);
             break;
         case SINET_STRAT_PRIV_TILE:
-        case SINET_STRAT_SMEM_FULL: {
-            TileArgs ta{};
-            LaunchCfg ct = c;
-            ct.block = p->block_threads ? (int)p->block_threads : 512;
-            // chunks of at most 8,192 records keep a bin's count within the
-            // 14 bits of a packed tile entry
-            ta.iters = (uint32_t)(2048 / ct.block);
-            if (ta.iters == 0) ta.iters = 1;
-            if (strat == SINET_STRAT_SMEM_FULL) {
-                if (p->n_bins > cap) return SINET_ERR_UNSUPPORTED;
-                ta.tile_bins = (uint32_t)p->n_bins;
-                ta.full = 1;
-                ta.margin = 0;
-            } else {
-                uint32_t T = p->tile_bins ? p->tile_bins : 4096;
-                if (T > cap) T = cap & ~255u;
-                if (T == 0) return SINET_ERR_UNSUPPORTED;
-                ta.tile_bins = T;
-                ta.full = 0;
-                ta.margin = T / 6;
-            }
+        case SINET_STRAT_SMEM_FULL:
             e = run_fused_tile(lk, r, ta_tab, h, ta, ct);
             break;
-        }
-        case SINET_STRAT_OWNER: {
-            OwnerArgs oa{};
-            LaunchCfg co = c;
-            co.block = p->block_threads ? (int)p->block_threads : 512;
-            oa.iters = (uint32_t)(2048 / co.block);
-            if (oa.iters == 0) oa.iters = 1;
-            uint32_t T = p->tile_bins ? p->tile_bins : 4096;
-            if (T > cap) T = cap & ~255u;
-            if (T == 0) return SINET_ERR_UNSUPPORTED;
-            oa.tile_bins = T;
-            oa.margin = T / 6;
-            oa.accumulate = p->accumulate ? 1u : 0u;
-            const uint64_t qpc = (uint64_t)co.block * oa.iters;
-            const uint64_t n_chunks = (r.g.quads + qpc - 1) / qpc;
-            const size_t bytes = 256 + 8 * n_chunks + 4 * n_chunks;
-            void *scratch = nullptr;
-            e = cudaMallocAsync(&scratch, bytes, s);
-            if (e != cudaSuccess) return cuda_fail(e);
-            e = cudaMemsetAsync(scratch, 0, bytes, s);
-            oa.ticket = static_cast<uint64_t *>(scratch);
-            oa.words = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(scratch) + 256);
-            oa.done = reinterpret_cast<uint32_t *>(oa.words + n_chunks);
-            if (e == cudaSuccess) e = run_fused_owner(lk, r, ta_tab, h, oa, co);
-            cudaError_t e2 = cudaFreeAsync(scratch, s);
-            if (e == cudaSuccess) e = e2;
-            break;
-        }
         case SINET_STRAT_SORT_REDUCE: {
-            if (r.g.n * (h.two_dir ? 2ull : 1ull) >= 0xFFFFFFF0ull) return SINET_ERR_UNSUPPORTED;
             SortPlan plan = plan_sort_reduce(r.g.n, h.n_bins, h.two_dir);
             void *scratch = nullptr;
             e = cudaMallocAsync(&scratch, plan.scratch_bytes, s);
@@ -279,7 +272,7 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
             break;
         }
         default:
-            return SINET_ERR_INVALID_ARG;
+            e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return cuda_fail(e);
     return SINET_OK;
@@ -387,6 +380,7 @@ sinet_status sinet_build_prefix_table(const uint32_t *h_net, const uint8_t *h_le
     a.off_blocks = t->img.off_blocks;
     a.off_desc = t->img.off_desc;
     a.desc_bits = t->host.desc_bits;
+    a.toggle_form = t->host.toggle_form;
     a.off_lo = t->img.off_lo;
     a.off_hi = t->img.off_hi;
     a.off_idx32 = t->img.off_idx32;

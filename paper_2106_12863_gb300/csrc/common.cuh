@@ -3,7 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/sinet.h"
+#include "sinet.h"
 
 namespace sinet {
 
@@ -198,16 +198,25 @@ struct PmlView {
 
 // Toggle form (shared memory). For the bucket of the top `bits` address bits,
 // desc gives the membership of the bucket's first address (bit 31) and the
-// blocks (bits 0-23 first, bits 24-27 count) holding the ascending offsets at
-// which membership flips; an address is inside when the start state XOR the
-// parity of the toggles at or below its offset is 1. Pure buckets use block 0
-// (all 0xFFFFFFFF, above every offset), so the first block load is
-// unconditional and the lookup has no data-dependent branch.
+// blocks holding the ascending offsets t at which membership flips, stored as
+// t - 1 (< 2^24; padded with 0x7FFFFFFF): NB = 1, one block (bits 0-14);
+// NB = 2, two blocks (bits 0-14, 15-29; the second may be the all-padding
+// block 0); NB = 0, consecutive blocks (bits 0-23 first, 24-27 count). A
+// toggle lies at or below the address's offset `off` exactly when
+// (t - 1) - off is negative as a 32-bit signed value, so the XOR of the four
+// differences (and of desc, for the start state) carries the membership in
+// bit 31. Pure buckets use block 0, so for NB = 1, 2 every lookup is the same
+// branch-free sequence of loads and integer operations.
+template <int NB>  // 1 or 2 blocks per bucket, loaded unconditionally; 0: as counted
 struct ToggleView {
     const uint4 *blocks;
     const uint32_t *desc;
     uint32_t shift;     // 32 - bits
     uint32_t off_mask;  // (1 << shift) - 1
+
+    static __device__ __forceinline__ uint32_t parity_bits(const uint4 &b, uint32_t off) {
+        return (b.x - off) ^ (b.y - off) ^ (b.z - off) ^ (b.w - off);
+    }
 
     template <int N>
     __device__ __forceinline__ void contains_n(const uint32_t (&a)[N], uint32_t (&in)[N]) const {
@@ -217,17 +226,19 @@ struct ToggleView {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const uint32_t off = a[i] & off_mask;
-            const uint4 b = blocks[d[i] & 0xFFFFFFu];
-            in[i] = (d[i] >> 31) ^ (off >= b.x) ^ (off >= b.y) ^ (off >= b.z) ^ (off >= b.w);
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const uint32_t nb = (d[i] >> 24) & 0xFu;
-            const uint32_t off = a[i] & off_mask;
-            for (uint32_t k = 1; k < nb; ++k) {
-                const uint4 b = blocks[(d[i] & 0xFFFFFFu) + k];
-                in[i] ^= (off >= b.x) ^ (off >= b.y) ^ (off >= b.z) ^ (off >= b.w);
+            uint32_t x;
+            if (NB == 0) {
+                const uint4 *bp = blocks + (d[i] & 0xFFFFFFu);
+                x = parity_bits(bp[0], off) ^ d[i];
+                if (d[i] & 0x0E000000u) {  // more than one block (rare)
+                    const uint32_t nb = (d[i] >> 24) & 0xFu;
+                    for (uint32_t k = 1; k < nb; ++k) x ^= parity_bits(bp[k], off);
+                }
+            } else {
+                x = parity_bits(blocks[d[i] & 0x7FFFu], off) ^ d[i];
+                if (NB == 2) x ^= parity_bits(blocks[(d[i] >> 15) & 0x7FFFu], off);
             }
+            in[i] = x >> 31;
         }
     }
 };
@@ -236,7 +247,7 @@ struct ToggleView {
 struct TableArgs {
     const uint8_t *image;     // device image base
     uint32_t iv_bytes;        // [blocks | desc] staged for the toggle form
-    uint32_t off_blocks, off_desc, desc_bits;
+    uint32_t off_blocks, off_desc, desc_bits, toggle_form;
     uint32_t off_lo, off_hi, off_idx32;  // global-memory interval form
     uint32_t n_iv, index_bits;
     uint32_t off_nets, off_groups, pml_bytes, n_groups;

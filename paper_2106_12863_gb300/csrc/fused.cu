@@ -302,6 +302,8 @@ __global__ void __launch_bounds__(1024) k_fused_tile(RecArgs r, TableArgs t, His
         __syncthreads();
         const uint32_t lo = s_lo, hi = s_hi;
         if (lo <= hi) {
+            // consecutive lanes take consecutive bins, so each warp-wide global
+            // atomic covers as few sectors as possible
             const uint32_t n = hi - lo + 1;
             for (uint32_t i = threadIdx.x; i < 2 * n; i += blockDim.x) {
                 const uint32_t d = i >= n;
@@ -364,6 +366,8 @@ cudaError_t run_discriminate(int lk, const RecArgs &r, const TableArgs &t, uint6
         break;                                                                                  \
     }
         SINET_DISC(LK_INTERVAL)
+        SINET_DISC(LK_TOGGLE1)
+        SINET_DISC(LK_TOGGLE2)
         SINET_DISC(LK_PML)
         SINET_DISC(LK_INTERVAL_GLOBAL)
 #undef SINET_DISC
@@ -387,6 +391,10 @@ cudaError_t run_fused_atomic(int lk, bool agg, const RecArgs &r, const TableArgs
     }
     SINET_ATOM(LK_INTERVAL, true)
     SINET_ATOM(LK_INTERVAL, false)
+    SINET_ATOM(LK_TOGGLE1, true)
+    SINET_ATOM(LK_TOGGLE1, false)
+    SINET_ATOM(LK_TOGGLE2, true)
+    SINET_ATOM(LK_TOGGLE2, false)
     SINET_ATOM(LK_PML, true)
     SINET_ATOM(LK_PML, false)
     SINET_ATOM(LK_INTERVAL_GLOBAL, true)
@@ -411,6 +419,10 @@ cudaError_t run_fused_tile(int lk, const RecArgs &r, const TableArgs &t, const H
     }
     SINET_TILE(LK_INTERVAL, true)
     SINET_TILE(LK_INTERVAL, false)
+    SINET_TILE(LK_TOGGLE1, true)
+    SINET_TILE(LK_TOGGLE1, false)
+    SINET_TILE(LK_TOGGLE2, true)
+    SINET_TILE(LK_TOGGLE2, false)
     SINET_TILE(LK_PML, true)
     SINET_TILE(LK_PML, false)
     SINET_TILE(LK_INTERVAL_GLOBAL, true)

@@ -34,20 +34,6 @@ cudaError_t run_fused_atomic(int lk, bool agg, const RecArgs &r, const TableArgs
 cudaError_t run_fused_tile(int lk, const RecArgs &r, const TableArgs &t, const HistArgs &h,
                            const TileArgs &ta, const LaunchCfg &c);
 
-struct OwnerArgs {
-    uint64_t *words;      // per chunk: flags (bits 62-63) | largest bin touched + 1
-    uint32_t *done;       // per chunk: 1 once its own bins are stored
-    uint64_t *ticket;     // chunk ticket counter
-    uint32_t tile_bins;   // bins per direction in the tile
-    uint32_t iters;       // quads per thread per chunk (chunk <= 8,192 records)
-    uint32_t margin;      // bins kept below a chunk's first record
-    uint32_t accumulate;  // add to the existing histogram instead of overwriting it
-};
-
-// Fused discriminate + histogram writing each bin once (time-sorted input).
-cudaError_t run_fused_owner(int lk, const RecArgs &r, const TableArgs &t, const HistArgs &h,
-                            const OwnerArgs &oa, const LaunchCfg &c);
-
 // Largest dynamic shared memory a CTA may use on this device.
 size_t smem_optin_limit();
 

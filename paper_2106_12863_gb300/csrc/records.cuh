@@ -6,7 +6,10 @@
 
 namespace sinet {
 
-enum : int { LK_INTERVAL = 0, LK_PML = 1, LK_INTERVAL_GLOBAL = 2, LK_CLASS_IN = 3 };
+// Lookup kinds: LK_INTERVAL / LK_TOGGLE1 / LK_TOGGLE2 are the shared-memory
+// toggle form with a variable / one / two blocks per bucket.
+enum : int { LK_INTERVAL = 0, LK_PML = 1, LK_INTERVAL_GLOBAL = 2, LK_CLASS_IN = 3, LK_TOGGLE1 = 4,
+             LK_TOGGLE2 = 5 };
 
 struct RecArgs {
     const uint64_t *ts;
@@ -29,6 +32,7 @@ struct HistArgs {
     uint32_t policy;  // byte c = direction bits of class c
     uint32_t two_dir; // some class routes to both directions
     uint32_t n_bins;
+    uint32_t *status;  // device status word
 };
 
 // ---------------------------------------------------------------------------
@@ -37,9 +41,9 @@ struct HistArgs {
 template <int LK>
 struct Classifier;
 
-template <>
-struct Classifier<LK_INTERVAL> {
-    ToggleView v;
+template <int NB>
+struct ToggleClassifier {
+    ToggleView<NB> v;
     __device__ __forceinline__ void init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
                                          uint32_t *status) {
         stage_to_smem(smem, t.image, t.iv_bytes, bar, status);
@@ -51,9 +55,15 @@ struct Classifier<LK_INTERVAL> {
     static __host__ __device__ uint32_t smem_bytes(const TableArgs &t) { return t.iv_bytes; }
     template <int N>
     __device__ __forceinline__ void in_n(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
-        v.contains_n<N>(a, r);
+        v.template contains_n<N>(a, r);
     }
 };
+template <>
+struct Classifier<LK_INTERVAL> : ToggleClassifier<0> {};
+template <>
+struct Classifier<LK_TOGGLE1> : ToggleClassifier<1> {};
+template <>
+struct Classifier<LK_TOGGLE2> : ToggleClassifier<2> {};
 
 template <>
 struct Classifier<LK_PML> {
@@ -113,15 +123,8 @@ struct Quad {
 // Load quad q with the fields the caller needs.
 template <bool TS, bool ADDR, bool BY, bool CIN>
 __device__ __forceinline__ void load_quad(const RecArgs &r, uint64_t q, uint64_t pol, Quad &Q) {
-    Q.valid = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        Q.ts[j] = 0;
-        Q.src[j] = Q.dst[j] = Q.by[j] = Q.cls[j] = 0;
-    }
-    if (q >= r.g.quads) return;
     const int64_t base = quad_base(r.g, q);
-    if (quad_full(r.g, base)) {
+    if (q < r.g.quads && quad_full(r.g, base)) {
         if (TS) {
             ulonglong2 a = ld_stream_v2u64(r.ts + base, pol);
             ulonglong2 b = ld_stream_v2u64(r.ts + base + 2, pol);
@@ -144,10 +147,15 @@ __device__ __forceinline__ void load_quad(const RecArgs &r, uint64_t q, uint64_t
         Q.valid = 0xFu;
         return;
     }
+    // partial quad (head, tail, unaligned streams) or past the end: scalar
+    // loads of the records that exist, zeros elsewhere
+    Q.valid = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+        Q.ts[j] = 0;
+        Q.src[j] = Q.dst[j] = Q.by[j] = Q.cls[j] = 0;
         const int64_t i = base + j;
-        if (i < 0 || (uint64_t)i >= r.g.n) continue;
+        if (q >= r.g.quads || i < 0 || (uint64_t)i >= r.g.n) continue;
         Q.valid |= 1u << j;
         if (TS) Q.ts[j] = ld_stream_u64(r.ts + i, pol);
         if (ADDR) {
@@ -310,3 +318,4 @@ __device__ __forceinline__ void gadd(const HistArgs &h, uint32_t d, uint32_t bin
 }
 
 }  // namespace sinet
+

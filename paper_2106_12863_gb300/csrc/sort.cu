@@ -466,7 +466,7 @@ cudaError_t run_sort_reduce(int lk, const RecArgs &r, const TableArgs &t, const 
     if (e != cudaSuccess) return e;
     if (r.g.quads == 0) return cudaSuccess;
 
-    const uint32_t tsm = (lk == LK_INTERVAL ? Classifier<LK_INTERVAL>::smem_bytes(t)
+    const uint32_t tsm = (lk == LK_INTERVAL || lk == LK_TOGGLE1 || lk == LK_TOGGLE2 ? Classifier<LK_INTERVAL>::smem_bytes(t)
                           : lk == LK_PML    ? Classifier<LK_PML>::smem_bytes(t)
                                             : 0u);
     const size_t smem = ((tsm + 15u) & ~15u) + 8ull * kEmitRecords * (h.two_dir ? 2 : 1);
@@ -479,6 +479,8 @@ cudaError_t run_sort_reduce(int lk, const RecArgs &r, const TableArgs &t, const 
                                                                               plan.emit_tiles, c.status); \
         break;
         SINET_EMIT(LK_INTERVAL)
+        SINET_EMIT(LK_TOGGLE1)
+        SINET_EMIT(LK_TOGGLE2)
         SINET_EMIT(LK_PML)
         SINET_EMIT(LK_INTERVAL_GLOBAL)
         SINET_EMIT(LK_CLASS_IN)

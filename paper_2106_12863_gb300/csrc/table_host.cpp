@@ -13,7 +13,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "../../include/sinet.h"
+#include "sinet.h"
 #include "table_host.h"
 
 namespace sinet {
@@ -113,11 +113,13 @@ int compile_table(const uint32_t *net, const uint8_t *len, uint32_t n, uint32_t 
     t.index_bits = k;
     t.max_range = build_index(k);
 
-    // toggle form: the fewest bits (8..14) whose buckets hold at most 8
-    // toggles (two blocks) and whose image fits the shared-memory budget
-    auto build_toggles = [&](uint32_t kb, bool keep) {
+    // toggle form `form` (1, 2 or 0, see table_host.h) at kb bucket bits;
+    // returns (most blocks one bucket needs, image bytes), or ~0 when the form
+    // cannot hold this table
+    auto build_toggles = [&](uint32_t kb, uint32_t form, bool keep) {
         const uint32_t nb = 1u << kb;
-        std::vector<uint32_t> desc(nb, 0), blocks(4, 0xFFFFFFFFu);
+        const auto fail = std::pair<uint32_t, size_t>(~0u, ~size_t(0));
+        std::vector<uint32_t> desc(nb, 0), blocks(4, 0x7FFFFFFFu);
         uint32_t maxb = 1, j = 0;
         std::vector<uint32_t> tog;
         for (uint32_t b = 0; b < nb; b++) {
@@ -130,15 +132,24 @@ int compile_table(const uint32_t *net, const uint8_t *len, uint32_t n, uint32_t 
                 if ((uint64_t)t.lo[e] > start) tog.push_back((uint32_t)((uint64_t)t.lo[e] - start));
                 if ((uint64_t)t.hi[e] < end) tog.push_back((uint32_t)((uint64_t)t.hi[e] + 1 - start));
             }
-            uint32_t nblk = 1, first = 0;
-            if (!tog.empty()) {
-                nblk = (uint32_t)(tog.size() + 3) / 4;
+            const uint32_t need = (uint32_t)(tog.size() + 3) / 4;
+            maxb = std::max(maxb, need ? need : 1u);
+            uint32_t first = 0;
+            if (need) {
                 first = (uint32_t)blocks.size() / 4;
-                for (uint32_t i = 0; i < nblk * 4; i++) blocks.push_back(i < tog.size() ? tog[i] : 0xFFFFFFFFu);
+                for (uint32_t i = 0; i < need * 4; i++) blocks.push_back(i < tog.size() ? tog[i] - 1 : 0x7FFFFFFFu);
             }
-            maxb = std::max(maxb, nblk);
-            if (nblk > 15 || first > 0xFFFFFFu) return std::pair<uint32_t, size_t>(~0u, ~size_t(0));
-            desc[b] = first | (nblk << 24) | (s0 << 31);
+            if (form == 1) {
+                if (need > 1 || first > 0x7FFFu) return fail;
+                desc[b] = first | (s0 << 31);
+            } else if (form == 2) {
+                if (need > 2 || first + 1 > 0x7FFFu) return fail;
+                desc[b] = first | ((need == 2 ? first + 1 : 0u) << 15) | (s0 << 31);
+            } else {
+                const uint32_t nblk = need ? need : 1u;
+                if (nblk > 15 || first > 0xFFFFFFu) return fail;
+                desc[b] = first | (nblk << 24) | (s0 << 31);
+            }
         }
         const size_t bytes = 4 * blocks.size() + 4 * (size_t)nb;
         if (keep) {
@@ -146,19 +157,36 @@ int compile_table(const uint32_t *net, const uint8_t *len, uint32_t n, uint32_t 
             t.blocks.swap(blocks);
             t.desc_bits = kb;
             t.max_blocks = maxb;
+            t.toggle_form = form;
         }
         return std::pair<uint32_t, size_t>(maxb, bytes);
     };
-    uint32_t kb = 0, fallback = 0;
-    size_t fallback_bytes = ~size_t(0);
-    for (uint32_t c = 8; c <= 14 && !kb; c++) {
-        auto r = build_toggles(c, false);
-        if (r.first == ~0u || r.second > kSmemTableBudget) continue;
-        if (r.first <= 2) kb = c;
-        else if (r.second < fallback_bytes) { fallback = c; fallback_bytes = r.second; }
+    // one block per bucket if some bit count allows it, else two, else as
+    // many as needed; within a form, the fewest bits that fit the budget
+    uint32_t kb = 0, form = 0;
+    for (uint32_t f : {1u, 2u}) {
+        for (uint32_t c = 8; c <= 14 && !kb; c++) {
+            auto r = build_toggles(c, f, false);
+            if (r.first != ~0u && r.second <= kSmemTableBudget) {
+                kb = c;
+                form = f;
+            }
+        }
+        if (kb) break;
     }
-    if (!kb) kb = fallback ? fallback : 14;
-    build_toggles(kb, true);
+    if (!kb) {
+        size_t best = ~size_t(0);
+        for (uint32_t c = 8; c <= 14; c++) {
+            auto r = build_toggles(c, 0, false);
+            if (r.first != ~0u && r.second < best) {
+                best = r.second;
+                kb = c;
+            }
+        }
+        if (!kb) kb = 14;
+        form = 0;
+    }
+    build_toggles(kb, form, true);
     return SINET_OK;
 }
 
@@ -248,8 +276,8 @@ extern "C" sinet_status sinet_prefix_table_image(const uint32_t *h_net, const ui
     const uint32_t v[16] = {img.off_blocks, img.off_desc, t.desc_bits, img.iv_bytes,
                             img.off_nets, img.off_groups, (uint32_t)t.groups.size(), img.pml_bytes,
                             img.off_lo, img.off_hi, img.off_idx32, t.index_bits,
-                            (uint32_t)t.lo.size(), t.max_blocks, img.iv_fits_smem ? 1u : 0u,
-                            img.pml_fits_smem ? 1u : 0u};
+                            (uint32_t)t.lo.size(), t.max_blocks | (t.toggle_form << 8),
+                            img.iv_fits_smem ? 1u : 0u, img.pml_fits_smem ? 1u : 0u};
     std::memcpy(layout, v, sizeof v);
     if (image) {
         if (capacity < buf.size()) return SINET_ERR_INVALID_ARG;

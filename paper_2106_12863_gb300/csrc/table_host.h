@@ -18,17 +18,22 @@ struct TableHost {
     uint32_t index_bits = 0;
     std::vector<uint32_t> index;  // 2^index_bits + 1 entries
     uint32_t max_range = 0;       // largest candidate range of an index bucket
-    // toggle form for shared memory: for each bucket of the top desc_bits
-    // address bits, whether the bucket's first address is inside (bit 31), how
-    // many 4-offset blocks of toggles follow (bits 24-27) and where they start
-    // (bits 0-23). A toggle is the offset from the bucket start at which
-    // membership flips; membership of an address is the start state XOR the
-    // parity of the toggles at or below its offset. Block 0 is all sentinels
-    // (0xFFFFFFFF, never reached) and serves every pure bucket.
+    // toggle form for shared memory. A toggle is the offset t >= 1 from a
+    // bucket's start (bucket = the top desc_bits address bits) at which
+    // membership flips, stored as t - 1 in blocks of four (padded with the
+    // never-reached 0x7FFFFFFF); membership of an address is the state at the
+    // bucket start XOR the parity of the toggles at or below its offset. Block 0
+    // is all padding and serves pure buckets. Per-bucket descriptor, bit 31 =
+    // state at the bucket start, and:
+    //   form 1: bits 0-14 = the bucket's only block (at most 4 toggles)
+    //   form 2: bits 0-14 and 15-29 = its two blocks (at most 8 toggles; the
+    //           second is block 0 when four suffice)
+    //   form 0: bits 0-23 = first of consecutive blocks, bits 24-27 = count
     uint32_t desc_bits = 0;
     std::vector<uint32_t> desc;
     std::vector<uint32_t> blocks;  // 4 u32 per block
     uint32_t max_blocks = 0;       // most blocks one bucket needs
+    uint32_t toggle_form = 0;  // 1, 2 or 0 as described above
     // per-length groups in probe order (most covered addresses first)
     struct Group { uint32_t len, off, cnt; };
     std::vector<Group> groups;

@@ -194,16 +194,33 @@ def _toggle_lookup(img, lay, addrs):
     a = addrs.astype(np.uint64)
     d = desc[(a >> np.uint64(shift)).astype(np.int64)].astype(np.uint64)
     off = a & np.uint64((1 << shift) - 1)
-    first = (d & np.uint64(0xFFFFFF)).astype(np.int64)
-    nb = ((d >> np.uint64(24)) & np.uint64(0xF)).astype(np.int64)
-    assert nb.min() >= 1
-    assert (first + nb).max() <= len(blocks)  # every block read stays in the staged region
+    form = lay["max_blocks"] >> 8
+    if form == 0:  # consecutive blocks: first (bits 0-23), count (bits 24-27)
+        first = (d & np.uint64(0xFFFFFF)).astype(np.int64)
+        nb = ((d >> np.uint64(24)) & np.uint64(0xF)).astype(np.int64)
+        idx = [np.where(nb > k, first + k, -1) for k in range(int(nb.max()))]
+    else:  # one or two independent block indices (bits 0-14, 15-29)
+        idx = [(d & np.uint64(0x7FFF)).astype(np.int64)]
+        if form == 2:
+            idx.append(((d >> np.uint64(15)) & np.uint64(0x7FFF)).astype(np.int64))
+    for ix in idx:
+        assert ix.max() < len(blocks)  # every block read stays in the staged region
     state = (d >> np.uint64(31)).astype(np.uint8)
-    for k in range(int(nb.max())):
-        use = nb > k
-        b = blocks[np.where(use, first + k, 0)].astype(np.uint64)
-        par = ((off[:, None] >= b).sum(axis=1) & 1).astype(np.uint8)
+    for ix in idx:
+        use = ix >= 0
+        b = blocks[np.where(use, ix, 0)].astype(np.uint64)  # toggle offsets minus one
+        assert np.all(b < 2 ** 31)
+        par = ((off[:, None] >= b + np.uint64(1)).sum(axis=1) & 1).astype(np.uint8)
         state ^= np.where(use, par, 0).astype(np.uint8)
+    # the kernels' form: bit 31 of desc XOR every (stored - off) mod 2^32
+    x = d.copy()
+    for ix in idx:
+        use = ix >= 0
+        b = blocks[np.where(use, ix, 0)].astype(np.uint64)
+        diff = (b - off[:, None] + np.uint64(1 << 32)) & np.uint64(0xFFFFFFFF)
+        v = diff[:, 0] ^ diff[:, 1] ^ diff[:, 2] ^ diff[:, 3]
+        x ^= np.where(use, v, np.uint64(0))
+    assert np.array_equal(((x >> np.uint64(31)) & np.uint64(1)).astype(np.uint8), state)
     return state
 
 
@@ -220,14 +237,46 @@ def test_toggle_form_equals_oracle(orc, seed):
     assert np.array_equal(_toggle_lookup(img, lay, addrs), want)
 
 
+@pytest.mark.parametrize("want_form", [0, 1, 2])
+def test_toggle_forms_equal_oracle(orc, want_form):
+    """Tables built to need one block per bucket, two, or a variable count."""
+    rng = random.Random(7 + want_form)
+    base = 0x0A000000
+    if want_form == 1:
+        net = [base + (i << 20) for i in range(8)]
+        ln = [16] * 8
+    elif want_form == 2:   # 5-8 toggles crowd one /14 bucket
+        net = [base + (i << 12) for i in range(4)]
+        ln = [24] * 4
+    else:                  # twenty /32 hosts in one /14 bucket
+        net = [base + 7 * i for i in range(20)]
+        ln = [32] * 20
+    net, ln = np.array(net, np.uint32), np.array(ln, np.uint8)
+    img, lay = sinet.sinet_prefix_table_image(net, ln)
+    assert lay["iv_fits_smem"] == 1 and lay["max_blocks"] >> 8 == want_form
+    addrs = np.concatenate([_edge_addrs(net, ln, rng, 2000),
+                            np.arange(base - 8, base + 400, dtype=np.uint32)])
+    want = orc.classify(net, ln, addrs, np.zeros_like(addrs)) & 1
+    assert np.array_equal(_toggle_lookup(img, lay, addrs), want)
+
+
 def test_toggle_form_on_workload_tables(orc):
     rng = random.Random(9)
     for key in ("tiny", "day", "heavy"):
         w = gen.WORKLOADS[key]
         net, ln = gen.make_table(w.table, w.seed)
         img, lay = sinet.sinet_prefix_table_image(net, ln)
-        assert lay["iv_fits_smem"] == 1 and lay["max_blocks"] <= 2
+        assert lay["iv_fits_smem"] == 1 and (lay["max_blocks"] & 0xFF) <= 2
         r = gen.make_records(gen.scaled(w, 50_000).records, w.seed, net, ln)
         addrs = np.concatenate([r["src"], r["dst"], _edge_addrs(net[:200], ln[:200], rng, 2000)])
         want = orc.classify(net, ln, addrs, np.zeros_like(addrs)) & 1
         assert np.array_equal(_toggle_lookup(img, lay, addrs), want)
+
+
+def test_too_dense_bucket_uses_global_intervals():
+    """A bucket needing more than 15 toggle blocks at every bucket width: the
+    shared-memory form is not offered (lookups use global-memory intervals)."""
+    net = np.array([0x0A000000 + 7 * i for i in range(80)], np.uint32)
+    ln = np.full(80, 32, np.uint8)
+    img, lay = sinet.sinet_prefix_table_image(net, ln)
+    assert lay["iv_fits_smem"] == 0

@@ -24,7 +24,7 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU too
 
 import paper_2106_12863_gb300 as sinet  # noqa: E402
 
-STRATS = ["global_atomic", "atomic_noagg", "priv_tile", "owner", "sort_reduce"]
+STRATS = ["global_atomic", "atomic_noagg", "priv_tile", "sort_reduce"]
 POLICIES = {"exclusive": sinet.EXCLUSIVE, "inclusive": sinet.INCLUSIVE, "paper_alg1": sinet.PAPER_ALG1}
 
 
@@ -74,7 +74,7 @@ def _disc_inputs(net, ln, n, seed):
 
 
 @pytest.mark.parametrize("lookup", ["interval", "pml"])
-@pytest.mark.parametrize("table", ["tiny", "day", "heavy", "edges", "empty", "slash0"])
+@pytest.mark.parametrize("table", ["tiny", "day", "heavy", "edges", "empty", "slash0", "dense", "dense80"])
 def test_discriminate_parity(orc, lookup, table):
     if table in gen.WORKLOADS:
         w = gen.WORKLOADS[table]
@@ -83,6 +83,10 @@ def test_discriminate_parity(orc, lookup, table):
         net, ln = _edge_table(5)
     elif table == "empty":
         net, ln = np.zeros(0, np.uint32), np.zeros(0, np.uint8)
+    elif table in ("dense", "dense80"):  # many /32 hosts in one bucket (variable / global forms)
+        k = 20 if table == "dense" else 80
+        net = np.array([0x0A000000 + 7 * i for i in range(k)], np.uint32)
+        ln = np.full(k, 32, np.uint8)
     else:
         net, ln = np.array([0x0A000000, 0xC0A80000], np.uint32), np.array([0, 16], np.uint8)
     n = 200_003
