@@ -248,6 +248,73 @@ sinet_status sinet_discriminate_histogram_noalloc(const sinet_prefix_table *t, c
                                                   const sinet_hist_params *p,
                                                   const sinet_hist_out *o, sinet_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched persistent launch (Section 4's coordinated batches: many chunks,
+ * each discriminated and reduced, their outputs kept apart).
+ *
+ * A batch is a fixed set of independent slices, each with its own records,
+ * prefix table, window, bin width, class policy and outputs. One launch of
+ * one persistent kernel processes all of them: its CTAs pull (slice, chunk)
+ * work items from a device counter, restage a slice's table into shared
+ * memory when it differs from the one they hold, and update the slice's
+ * histogram with the strategy chosen for it. The launch (a zeroing kernel
+ * for non-accumulating slices, then the batch kernel) is captured once as a
+ * CUDA graph at creation; sinet_batch_run replays it.
+ */
+typedef struct {
+    const uint64_t *ts;               /* device records, as in sinet_discriminate_histogram */
+    const uint32_t *src;
+    const uint32_t *dst;
+    const uint32_t *bytes;
+    uint64_t n;
+    const sinet_prefix_table *table;  /* must outlive the batch */
+    sinet_hist_params params;         /* strategy: AUTO, GLOBAL_ATOMIC, ATOMIC_NOAGG or SMEM_FULL;
+                                         lookup: AUTO or INTERVAL; hints, tile_bins and
+                                         block_threads are ignored */
+    sinet_hist_out out;               /* device outputs; must outlive the batch */
+} sinet_batch_slice;
+
+/* Flags of sinet_batch_create. */
+#define SINET_BATCH_AUTOTUNE 1u /* time the candidate strategies of AUTO slices (see below) */
+
+typedef struct sinet_batch sinet_batch;
+
+/*
+ * Validate and plan n_slices slices (1 <= n_slices <= 65,536), upload their
+ * descriptors and capture the launch. Slices with strategy AUTO get one from
+ * the autotuner: slices are grouped into classes (lookup form, whether the
+ * histogram fits a shared-memory tile, log2 of n_bins and of n, unit bin
+ * width, both-direction policy); with SINET_BATCH_AUTOTUNE, each class not
+ * yet in the process-wide cache is tuned by timing every candidate strategy
+ * on its largest slice (its first 8 M records at most, into scratch outputs:
+ * the slice's own outputs are not touched), and the fastest is cached and, if
+ * the environment variable SINET_AUTOTUNE_CACHE names a file, appended to it
+ * (the file is read on first use). Without the flag a class absent from the
+ * cache takes a fixed rule. Tuning runs on `stream` and synchronises it.
+ * The records, tables and outputs are referenced, not copied: they must
+ * stay valid, and the records unchanged between runs only if the caller
+ * wants the same result. Returns SINET_ERR_INVALID_ARG for a NULL slice
+ * array, table or output, misaligned pointers or bad params (as
+ * sinet_discriminate_histogram), SINET_ERR_UNSUPPORTED for a strategy or
+ * lookup the batch kernel does not run, or SMEM_FULL for a histogram that
+ * does not fit a tile.
+ */
+sinet_status sinet_batch_create(const sinet_batch_slice *slices, uint32_t n_slices, uint32_t flags,
+                                sinet_stream_t stream, sinet_batch **out);
+
+/* Enqueue one run of the batch on `stream` (a graph launch). Non-accumulating
+ * slices' outputs are zeroed first; accumulating slices are added to. */
+sinet_status sinet_batch_run(sinet_batch *b, sinet_stream_t stream);
+
+/* The strategy (sinet_strategy) the batch runs for slice i, after tuning. */
+sinet_status sinet_batch_strategy(const sinet_batch *b, uint32_t i, int32_t *strategy);
+
+/* Work items and records of the batch (either pointer may be NULL). */
+sinet_status sinet_batch_info(const sinet_batch *b, uint64_t *work_items, uint64_t *records);
+
+/* Synchronise the device, then free the batch (NULL is a no-op). */
+sinet_status sinet_batch_destroy(sinet_batch *b);
+
 /*
  * Read and clear the device status word of the current device, after
  * synchronising `stream`. *device_code receives the latched sinet_status

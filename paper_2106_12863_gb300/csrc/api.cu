@@ -9,30 +9,17 @@
 
 namespace sinet {
 
-struct DeviceState {
-    bool ready = false;
-    int sm_count = 0;
-    size_t smem_optin = 0;
-    size_t smem_per_sm = 0;
-    uint32_t *status = nullptr;  // device status word
-};
-
 static std::mutex g_mu;
 static DeviceState g_dev[64];
 static thread_local int t_last_cuda = 0;
 
-static sinet_status cuda_fail(cudaError_t e) {
+sinet_status cuda_fail(cudaError_t e) {
     t_last_cuda = (int)e;
     return e == cudaErrorMemoryAllocation ? SINET_ERR_OOM : SINET_ERR_CUDA;
 }
 
-#define SINET_CUDA(x)                                   \
-    do {                                                \
-        cudaError_t e_ = (x);                           \
-        if (e_ != cudaSuccess) return cuda_fail(e_);    \
-    } while (0)
 
-static sinet_status device_state(DeviceState **out) {
+sinet_status device_state(DeviceState **out) {
     int dev = 0;
     SINET_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return SINET_ERR_UNSUPPORTED;

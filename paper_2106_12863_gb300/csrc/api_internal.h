@@ -17,6 +17,24 @@ namespace sinet {
 
 constexpr uint64_t kMaxN = 1ull << 40;
 
+// Per-device facts and the device status word, set up on first use.
+struct DeviceState {
+    bool ready = false;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    size_t smem_per_sm = 0;
+    uint32_t *status = nullptr;  // device status word
+};
+sinet_status device_state(DeviceState **out);
+// Map a failed CUDA call to a status (and remember it for sinet_last_cuda_error).
+sinet_status cuda_fail(cudaError_t e);
+
+#define SINET_CUDA(x)                                          \
+    do {                                                       \
+        cudaError_t e_ = (x);                                  \
+        if (e_ != cudaSuccess) return ::sinet::cuda_fail(e_);  \
+    } while (0)
+
 struct Stream {
     const void *p;
     uint32_t esize;

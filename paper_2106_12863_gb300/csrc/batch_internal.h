@@ -1,0 +1,61 @@
+// Host side of the batched launch, shared by the batch API and the serving
+// loop: slice planning, strategy resolution (the autotuner), and the device
+// engine that owns the descriptors and the captured graph.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace sinet {
+
+// Quads per work item: 64,000 records, below the 65,536 a tile entry counts.
+constexpr uint32_t kItemQuads = 16000;
+// Records a tuning run processes at most per candidate.
+constexpr uint64_t kTuneRecords = 8ull << 20;
+
+struct PlannedSlice {
+    BatchSlice d;
+    uint32_t items = 0;       // work items
+    uint32_t zero_items = 0;  // zeroing items (0 when accumulating)
+    int32_t strategy = 0;     // sinet_strategy; AUTO until resolved
+    bool tile_fits = false;   // the whole histogram fits a tile next to the table
+    uint32_t user_index = 0;  // position in the caller's slice array
+};
+
+// Dynamic shared memory of a batch CTA on this device (two CTAs per SM).
+uint32_t batch_smem(const DeviceState *ds);
+
+// Host-only checks of one slice (no CUDA call).
+sinet_status check_slice(const sinet_batch_slice &u);
+// Plan a checked slice for a batch kernel with `smem` bytes of shared memory.
+sinet_status plan_slice(const sinet_batch_slice &u, const DeviceState *ds, uint32_t smem, PlannedSlice &ps);
+// Give every AUTO slice a strategy: from the autotune cache, by timing the
+// candidates (tune), or by the fixed rule.
+sinet_status resolve_strategies(std::vector<PlannedSlice> &v, bool tune, const DeviceState *ds,
+                                uint32_t smem, cudaStream_t s);
+// Map a public strategy to the batch kernel's update scheme.
+uint32_t batch_scheme(int32_t strategy);
+
+// Device-resident descriptors + the captured launch.
+struct BatchEngine {
+    int device = 0;
+    uint32_t cap = 0;  // slices
+    uint32_t smem = 0;
+    int grid = 0, zgrid = 0;
+    void *d_mem = nullptr;
+    size_t bytes = 0;
+    size_t off_item = 0, off_zero = 0, off_slices = 0;
+    BatchArgs args{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    sinet_status init(uint32_t capacity, const DeviceState *ds, uint32_t smem_bytes);
+    // host image (header, starts, descriptors) of `v` in descriptor order
+    void image(const std::vector<PlannedSlice> &v, std::vector<uint8_t> &buf) const;
+    sinet_status capture(uint32_t *status);  // capture zero + batch kernels as a graph
+    sinet_status launch(cudaStream_t s) const;
+    void release();
+};
+
+}  // namespace sinet

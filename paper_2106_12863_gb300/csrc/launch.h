@@ -37,6 +37,63 @@ cudaError_t run_fused_tile(int lk, const RecArgs &r, const TableArgs &t, const H
 // Largest dynamic shared memory a CTA may use on this device.
 size_t smem_optin_limit();
 
+// ---------------------------------------------------------------------------
+// Batched persistent launch: many slices, each with its own records, table,
+// window, bin width and outputs, in one launch whose CTAs pull (slice, chunk)
+// work items from a device counter.
+
+// Histogram update of one slice inside the batch kernel.
+enum : uint32_t {
+    BS_AGG = 0,    // warp run-combining + per-CTA hot-key cache, then global atomics
+    BS_NOAGG = 1,  // global atomics per run of equal keys
+    BS_TILE = 2,   // the slice's whole histogram as a shared-memory tile per work item
+};
+
+struct BatchSlice {
+    RecArgs r;
+    TableArgs t;
+    HistArgs h;
+    uint32_t lk;         // LK_TOGGLE1, LK_TOGGLE2, LK_INTERVAL or LK_INTERVAL_GLOBAL
+    uint32_t strat;      // BS_*
+    uint32_t tile_bins;  // BS_TILE: bins per direction of the tile (>= n_bins, multiple of 4)
+    uint32_t zero;       // 1: the outputs are zeroed by the launch (not accumulated into)
+};
+
+// Device-resident header read by both batch kernels at every launch, so one
+// captured graph serves any slice set up to its capacity.
+struct BatchHeader {
+    uint32_t n_slices;
+    uint32_t item_quads;   // quads per work item
+    uint32_t total_items;  // work items of all slices
+    uint32_t total_zero;   // zeroing items of all slices
+    uint32_t counter;      // work-item counter, reset by the zeroing kernel
+    uint32_t pad[3];
+};
+
+// Device arrays of a batch (all device pointers).
+struct BatchArgs {
+    BatchHeader *hdr;
+    const BatchSlice *slices;
+    const uint32_t *item_start;  // [n_slices + 1] first work item of each slice
+    const uint32_t *zero_start;  // [n_slices + 1] first zeroing item of each slice
+};
+
+// Bins per zeroing item of the batch zeroing kernel.
+constexpr uint32_t kZeroBins = 1u << 16;
+// Hot-key cache of the batch kernel: 2^9 sets x 4 ways, 16 bytes a slot.
+constexpr uint32_t kBatchCacheSetBits = 9;
+constexpr uint32_t kBatchCacheBytes = 16u << (kBatchCacheSetBits + 2);
+// Threads of a batch CTA.
+constexpr int kBatchBlock = 512;
+
+// Zero the outputs of the slices marked `zero` and reset the work counter.
+cudaError_t run_batch_zero(const BatchArgs &b, int grid, cudaStream_t s);
+// The persistent batch kernel with `smem` bytes of dynamic shared memory per
+// CTA (table region + work region of any slice must fit).
+cudaError_t run_batch(const BatchArgs &b, uint32_t smem, int grid, cudaStream_t s, uint32_t *status);
+// Set the batch kernel's dynamic shared memory limit; returns CTAs per SM.
+cudaError_t batch_occupancy(uint32_t smem, int *per_sm);
+
 // Plain path: discriminate -> emit keys -> radix sort -> reduce by key.
 struct SortPlan {
     uint64_t n_emit_max;   // upper bound of emitted (key, bytes) pairs

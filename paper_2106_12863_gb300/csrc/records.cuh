@@ -47,6 +47,10 @@ struct ToggleClassifier {
     __device__ __forceinline__ void init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
                                          uint32_t *status) {
         stage_to_smem(smem, t.image, t.iv_bytes, bar, status);
+        attach(t, smem);
+    }
+    // views over an image already staged at `smem`
+    __device__ __forceinline__ void attach(const TableArgs &t, const uint8_t *smem) {
         v.blocks = reinterpret_cast<const uint4 *>(smem + t.off_blocks);
         v.desc = reinterpret_cast<const uint32_t *>(smem + t.off_desc);
         v.shift = 32 - t.desc_bits;
@@ -87,6 +91,9 @@ template <>
 struct Classifier<LK_INTERVAL_GLOBAL> {
     IntervalView<uint32_t> v;
     __device__ __forceinline__ void init(const TableArgs &t, uint8_t *, uint64_t *, uint32_t *) {
+        attach(t, nullptr);
+    }
+    __device__ __forceinline__ void attach(const TableArgs &t, const uint8_t *) {
         v.lo = reinterpret_cast<const uint32_t *>(t.image + t.off_lo);
         v.hi = reinterpret_cast<const uint32_t *>(t.image + t.off_hi);
         v.idx = reinterpret_cast<const uint32_t *>(t.image + t.off_idx32);

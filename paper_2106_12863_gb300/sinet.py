@@ -57,6 +57,14 @@ class HistOutC(ctypes.Structure):
                 ("stats", ctypes.c_void_p)]
 
 
+class BatchSliceC(ctypes.Structure):
+    _fields_ = [("ts", ctypes.c_void_p), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("bytes", ctypes.c_void_p), ("n", ctypes.c_uint64), ("table", ctypes.c_void_p),
+                ("params", HistParamsC), ("out", HistOutC)]
+
+
+BATCH_AUTOTUNE = 1
+
 _lib = None
 _P = ctypes.c_void_p
 
@@ -89,6 +97,11 @@ def load():
                                                                 ctypes.POINTER(HistParamsC),
                                                                 ctypes.POINTER(HistOutC), _P]),
         "sinet_device_status": (ctypes.c_int, [_P, _P]),
+        "sinet_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchSliceC), u32, u32, _P, _P]),
+        "sinet_batch_run": (ctypes.c_int, [_P, _P]),
+        "sinet_batch_strategy": (ctypes.c_int, [_P, u32, _P]),
+        "sinet_batch_info": (ctypes.c_int, [_P, _P, _P]),
+        "sinet_batch_destroy": (ctypes.c_int, [_P]),
         "sinet_default_params": (None, [ctypes.POINTER(HistParamsC), u64, u64, u64]),
     }
     for name, (res, args) in sig.items():
@@ -237,6 +250,36 @@ def sinet_device_status(stream=None) -> int:
     return int(v.value)
 
 
+def sinet_batch_create(slices, flags: int = 0, stream=None) -> int:
+    """``slices``: a sequence of BatchSliceC (kept alive by the caller)."""
+    arr = (BatchSliceC * len(slices))(*slices)
+    h = ctypes.c_void_p()
+    _check(load().sinet_batch_create(arr, len(slices), flags, _stream(stream), ctypes.byref(h)),
+           "sinet_batch_create")
+    return int(h.value)
+
+
+def sinet_batch_run(handle: int, stream=None):
+    _check(load().sinet_batch_run(handle, _stream(stream)), "sinet_batch_run")
+
+
+def sinet_batch_strategy(handle: int, i: int) -> int:
+    v = ctypes.c_int32()
+    _check(load().sinet_batch_strategy(handle, i, ctypes.byref(v)), "sinet_batch_strategy")
+    return int(v.value)
+
+
+def sinet_batch_info(handle: int):
+    items, records = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().sinet_batch_info(handle, ctypes.byref(items), ctypes.byref(records)),
+           "sinet_batch_info")
+    return int(items.value), int(records.value)
+
+
+def sinet_batch_destroy(handle: int):
+    _check(load().sinet_batch_destroy(handle), "sinet_batch_destroy")
+
+
 # ---------------------------------------------------------------------------
 # Conveniences
 
@@ -335,3 +378,45 @@ def discriminate_histogram(table: PrefixTable, ts, src, dst, nbytes, params: His
     sinet_discriminate_histogram(table.handle, ts, src, dst, nbytes, ts.numel(), params.c(),
                                  out.c(), stream)
     return out
+
+
+class Batch:
+    """A batch of independent slices run by one persistent graph-captured launch.
+
+    ``slices``: sequence of (table: PrefixTable, ts, src, dst, nbytes, params:
+    HistParams, out: Histogram). The tensors, tables and outputs are referenced
+    by the batch and kept alive here."""
+
+    def __init__(self, slices, autotune: bool = False, stream=None):
+        self._keep = list(slices)
+        cs = []
+        for table, ts, src, dst, nb, params, out in self._keep:
+            c = BatchSliceC()
+            c.ts, c.src, c.dst, c.bytes = _dptr(ts), _dptr(src), _dptr(dst), _dptr(nb)
+            c.n = ts.numel()
+            c.table = table.handle
+            c.params = params.c()
+            c.out = out.c()
+            cs.append(c)
+        self.handle = sinet_batch_create(cs, BATCH_AUTOTUNE if autotune else 0, stream)
+
+    def run(self, stream=None):
+        sinet_batch_run(self.handle, stream)
+
+    def strategy(self, i: int) -> str:
+        v = sinet_batch_strategy(self.handle, i)
+        return next(k for k, x in STRATEGIES.items() if x == v)
+
+    def info(self):
+        return sinet_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sinet_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

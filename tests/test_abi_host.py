@@ -186,6 +186,41 @@ def test_validation_rejects_before_any_cuda_call():
     assert L.sinet_discriminate(None, 0x40000, 0x50000, 8, None, 0x60000, 0, None) == 1
 
 
+def test_batch_validation_rejects_before_any_cuda_call():
+    """sinet_batch_create checks every slice on the host before touching a device."""
+    L = sinet.load()
+    h = ctypes.c_void_p()
+
+    def good():
+        c = sinet.BatchSliceC()
+        c.ts, c.src, c.dst, c.bytes, c.n, c.table = 0x40000, 0x50000, 0x60000, 0x70000, 8, 0x1000
+        c.params = sinet.HistParams(0, 1, 10).c()
+        for i in range(2):
+            c.out.count[i] = 0x10000
+            c.out.bytes[i] = 0x20000
+        c.out.stats = 0x30000
+        return c
+
+    def create(cs, flags=0):
+        arr = (sinet.BatchSliceC * max(len(cs), 1))(*cs)
+        return L.sinet_batch_create(arr if cs else None, len(cs), flags, None, ctypes.byref(h))
+
+    assert create([]) == 1
+    assert create([good()], flags=2) == 1
+    bad = []
+    c = good(); c.table = None; bad.append((c, 1))
+    c = good(); c.params.bin_width_ms = 0; bad.append((c, 1))
+    c = good(); c.ts = 0x40004; bad.append((c, 1))
+    c = good(); c.out.stats = None; bad.append((c, 1))
+    c = good(); c.params.strategy = sinet.STRAT_SORT_REDUCE; bad.append((c, 8))
+    c = good(); c.params.strategy = sinet.STRAT_PRIV_TILE; bad.append((c, 8))
+    c = good(); c.params.lookup = sinet.LOOKUP_PML; bad.append((c, 8))
+    for c, want in bad:
+        assert create([good(), c]) == want
+    assert L.sinet_batch_run(None, None) == 1
+    assert L.sinet_batch_destroy(None) == 0
+
+
 def _toggle_lookup(img, lay, addrs):
     """The shared-memory toggle lookup of the kernels, replayed on the host."""
     desc = img[lay["off_desc"]: lay["off_desc"] + 4 * (1 << lay["desc_bits"])].view(np.uint32)
