@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="day", choices=sorted(gen.WORKLOADS))
+    ap.add_argument("--workload", default="day", choices=sorted(gen.WORKLOADS) + ["batch"],
+                    help="day | heavy | tiny: one window; batch: 256 uneven slices in one "
+                         "persistent launch")
+    ap.add_argument("--slices", type=int, default=256, help="batch: number of slices")
     ap.add_argument("--records", type=int, default=0, help="override the record count")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink records, window and bins together (keeps records per bin; "
@@ -215,6 +218,9 @@ def run_reference(args):
     import oracle
 
     o = oracle.get()
+    if args.workload == "batch":
+        run_reference_batch(args, o)
+        return
     w = workload(args, rank)
     net, ln = gen.make_table(w.table, w.seed)
     # size each step's sample so that all warm-up + timed steps fit ~2.5 minutes
@@ -247,10 +253,260 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+class _OutView:
+    """Histogram outputs of one batch slice: views into flat device arrays."""
+
+    def __init__(self, count, nbytes, stats, off, nb, i):
+        self.count = count[2 * off: 2 * off + 2 * nb].view(2, nb)
+        self.bytes = nbytes[2 * off: 2 * off + 2 * nb].view(2, nb)
+        self.stats = stats[i]
+
+    def c(self):
+        import paper_2106_12863_gb300 as sinet
+
+        o = sinet.HistOutC()
+        o.count[0], o.count[1] = self.count[0].data_ptr(), self.count[1].data_ptr()
+        o.bytes[0], o.bytes[1] = self.bytes[0].data_ptr(), self.bytes[1].data_ptr()
+        o.stats = self.stats.data_ptr()
+        return o
+
+
+def run_batch_bench(args):
+    """256 uneven slices (own table, window, bin width each) as one batch:
+    the graph-captured persistent launch against one call per slice (fused and
+    plain)."""
+    rank, world, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2106_12863_gb300 as sinet
+
+    sinet.load()
+    plan = gen.batch_slices(n_slices=args.slices, seed=gen.BASE_SEED + 4 + 1000 * rank)
+    n_tot = sum(sp.n for sp in plan)
+    bins_tot = sum(sp.n_bins for sp in plan)
+    tg = time.perf_counter()
+    h = {"ts": torch.empty(n_tot, dtype=torch.int64, pin_memory=True),
+         "src": torch.empty(n_tot, dtype=torch.int32, pin_memory=True),
+         "dst": torch.empty(n_tot, dtype=torch.int32, pin_memory=True),
+         "bytes": torch.empty(n_tot, dtype=torch.int32, pin_memory=True)}
+    tables, offs, off = [], [], 0
+    for sp in plan:
+        net, ln = gen.make_table(sp.table, sp.seed)
+        gen.fill_records(sp.records, sp.seed, net, ln, 0, sp.n, h["ts"][off:off + sp.n],
+                         h["src"][off:off + sp.n], h["dst"][off:off + sp.n], h["bytes"][off:off + sp.n])
+        tables.append(sinet.PrefixTable(net, ln))
+        offs.append(off)
+        off += sp.n
+    t_gen = time.perf_counter() - tg
+    d = {k: v.to(dev) for k, v in h.items()}
+    count = torch.empty(2 * bins_tot, dtype=torch.int32, device=dev)
+    nbytes = torch.empty(2 * bins_tot, dtype=torch.int64, device=dev)
+    stats = torch.empty((len(plan), 8), dtype=torch.int64, device=dev)
+    outs, slices, boff = [], [], 0
+    for i, sp in enumerate(plan):
+        o = _OutView(count, nbytes, stats, boff, sp.n_bins, i)
+        boff += sp.n_bins
+        outs.append(o)
+        a, n = offs[i], sp.n
+        p = sinet.HistParams(sp.t0, sp.bin_width, sp.n_bins)
+        slices.append((tables[i], d["ts"][a:a + n], d["src"][a:a + n], d["dst"][a:a + n],
+                       d["bytes"][a:a + n], p, o))
+    stream = torch.cuda.current_stream(dev)
+    tt = time.perf_counter()
+    batch = sinet.Batch(slices, autotune=True)
+    t_tune = time.perf_counter() - tt
+    items, _ = batch.info()
+    strat_count = {}
+    for i in range(len(plan)):
+        s_ = batch.strategy(i)
+        strat_count[s_] = strat_count.get(s_, 0) + 1
+
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.mark(True)
+    t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_begin.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        batch.run()
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.mark(False)
+    clk = clocks.stop()
+    total_ms = t_begin.elapsed_time(t_end)
+    graph_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t_ = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t_.item())
+    ms_per_step = total_ms / args.steps
+    st = stats.cpu().numpy().view(np.uint64)
+    for i, sp in enumerate(plan):
+        assert int(st[i, :4].sum()) == sp.n, f"slice {i}: class counts do not sum to its records"
+    ref_stats = st.copy()
+
+    result = {"metric": METRIC, "value": world * n_tot * args.steps / (total_ms / 1e3), "unit": UNIT,
+              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "u32/u64",
+              "data": "synthetic (seeded generator; 256 uneven slices)"}
+    alg_bytes = RECORD_BYTES * n_tot + BIN_BYTES * bins_tot
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (graph_ms / 1e3) / 1e9
+    result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "traffic": None, "kernel": "k_batch_zero + k_batch",
+                          "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+                          "kernel_ms": graph_ms}
+    result["gpu_launches"] = 2 * args.steps  # zeroing kernel + batch kernel per graph replay
+    result["config"] = {"workload": f"batch-{len(plan)}-slices-uneven", "records": n_tot,
+                        "slices": len(plan), "bins_total": bins_tot, "work_items": items,
+                        "strategies": strat_count, "tune_s": round(t_tune, 2),
+                        "l2": f"inputs larger than L2 ({RECORD_BYTES * n_tot / 1e9:.1f} GB of records)",
+                        "policy": "exclusive", "parallelism": f"replicas x{world} (weak)",
+                        "gen_s": round(t_gen, 1)}
+    result["clocks"] = clk
+
+    def per_slice(strategy):
+        for i, sp in enumerate(plan):
+            t_, ts, src, dst, nb, _, o = slices[i]
+            sinet.discriminate_histogram(t_, ts, src, dst, nb,
+                                         sinet.HistParams(sp.t0, sp.bin_width, sp.n_bins,
+                                                          strategy=strategy), o)
+
+    for name, strategy, k in (("per_slice_fused", "auto", 3), ("per_slice_plain", "sort_reduce", 2)):
+        if name == "per_slice_plain" and args.no_plain:
+            continue
+        per_slice(strategy)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(k):
+            per_slice(strategy)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ms = p0.elapsed_time(p1) / k
+        result[name] = {"value": n_tot / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": k,
+                        "launches_per_step": len(plan)}
+        result[f"batched_vs_{name}"] = (n_tot / (ms_per_step / 1e3)) / result[name]["value"]
+        assert np.array_equal(stats.cpu().numpy().view(np.uint64), ref_stats), name
+
+    if not args.no_e2e:
+        hout = {"count": torch.empty_like(count, device="cpu").pin_memory(),
+                "bytes": torch.empty_like(nbytes, device="cpu").pin_memory(),
+                "stats": torch.empty_like(stats, device="cpu").pin_memory()}
+
+        def e2e_step():
+            for k_ in d:
+                d[k_].copy_(h[k_], non_blocking=True)
+            batch.run()
+            hout["count"].copy_(count, non_blocking=True)
+            hout["bytes"].copy_(nbytes, non_blocking=True)
+            hout["stats"].copy_(stats, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        q1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = q0.elapsed_time(q1) / args.e2e_steps
+        result["e2e"] = {"value": world * n_tot / (e2e_ms / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": sum(v.numel() * v.element_size() for v in h.values()),
+                         "d2h_bytes_per_step": sum(v.numel() * v.element_size() for v in hout.values()),
+                         "ms_per_step": e2e_ms, "steps": args.e2e_steps}
+        assert np.array_equal(hout["stats"].numpy().view(np.uint64), ref_stats)
+
+    if rank == 0 and not args.no_cpu:
+        import oracle
+
+        o_ = oracle.get()
+        done, t_cpu, i = 0, 0.0, 0
+        while t_cpu < args.cpu_seconds and i < len(plan):
+            sp = plan[i]
+            net, ln = gen.make_table(sp.table, sp.seed)
+            # a slice prefix at most as long as the remaining time allows at the rate so far
+            cap = sp.n if done == 0 else int(done / t_cpu * (args.cpu_seconds - t_cpu)) + 1
+            m = max(1, min(sp.n, cap, 200_000 if done == 0 else sp.n))
+            rec = gen.make_records(sp.records, sp.seed, net, ln, n=m)
+            t0_ = time.perf_counter()
+            o_.discriminate_histogram(net, ln, rec, sp.t0, sp.bin_width, sp.n_bins)
+            t_cpu += time.perf_counter() - t0_
+            done += m
+            i += 1
+        result["cpu_baseline"] = {"value": done / t_cpu, "unit": UNIT, "cores": o_.threads(),
+                                  "kind": "oracle",
+                                  "sample": f"prefixes of the first {i} slices of the batch "
+                                            f"({done} records), one oracle call per slice; "
+                                            f"{t_cpu:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    batch.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference_batch(args, o):
+    """The oracle on the batch workload: step s runs slice s (cyclically), on
+    a prefix sized so all steps fit about 2.5 minutes."""
+    plan = gen.batch_slices(n_slices=args.slices)
+    per_step = max(0.05, 150.0 / (args.steps + args.warmup))
+    sp = plan[0]
+    net, ln = gen.make_table(sp.table, sp.seed)
+    probe = min(50_000, sp.n)
+    rec = gen.make_records(sp.records, sp.seed, net, ln, n=probe)
+    t = time.perf_counter()
+    o.discriminate_histogram(net, ln, rec, sp.t0, sp.bin_width, sp.n_bins)
+    rate = probe / max(time.perf_counter() - t, 1e-6)
+    done, total = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        sp = plan[s % len(plan)]
+        net, ln = gen.make_table(sp.table, sp.seed)
+        m = max(1, min(sp.n, int(rate * per_step)))
+        rec = gen.make_records(sp.records, sp.seed, net, ln, n=m)
+        t = time.perf_counter()
+        o.discriminate_histogram(net, ln, rec, sp.t0, sp.bin_width, sp.n_bins)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            done += m
+            total += dt
+    value = done / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"batch-{len(plan)}-slices-uneven", "records_per_step": done // args.steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
+                             "sample": "a prefix of one slice per step, slices taken in order"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch_bench(args)
         return
     rank, world, local = dist_env()
     import torch

@@ -9,8 +9,12 @@
 
 namespace sinet {
 
-// Quads per work item: 64,000 records, below the 65,536 a tile entry counts.
+// Quads per work item: at most 64,000 records (below the 65,536 a tile entry
+// counts). Slices updated with global atomics get items small enough that the
+// whole grid works on one slice at a time (at least kMinItemQuads), so the
+// histograms under random read-modify-write stay few enough to share L2.
 constexpr uint32_t kItemQuads = 16000;
+constexpr uint32_t kMinItemQuads = 4096;
 // Records a tuning run processes at most per candidate.
 constexpr uint64_t kTuneRecords = 8ull << 20;
 
@@ -25,9 +29,15 @@ struct PlannedSlice {
 
 // Dynamic shared memory of a batch CTA on this device (two CTAs per SM).
 uint32_t batch_smem(const DeviceState *ds);
+// CTAs of the persistent batch grid (two per SM).
+uint32_t batch_grid(const DeviceState *ds);
 
 // Host-only checks of one slice (no CUDA call).
 sinet_status check_slice(const sinet_batch_slice &u);
+// Quads per work item of a slice run with scheme `scheme` by `grid` CTAs.
+uint32_t item_quads_for(uint64_t quads, uint32_t scheme, uint32_t grid);
+// Set the strategy of a planned slice (scheme, item size, item count).
+void set_strategy(PlannedSlice &ps, int32_t strategy, uint32_t grid);
 // Plan a checked slice for a batch kernel with `smem` bytes of shared memory.
 sinet_status plan_slice(const sinet_batch_slice &u, const DeviceState *ds, uint32_t smem, PlannedSlice &ps);
 // Give every AUTO slice a strategy: from the autotune cache, by timing the

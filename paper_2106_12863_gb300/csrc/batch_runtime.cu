@@ -13,12 +13,15 @@ namespace sinet {
 
 uint32_t batch_smem(const DeviceState *ds) {
     // two CTAs per SM; 1 KB per CTA is reserved by the hardware, and the
-    // kernel's static shared memory (descriptor copy, counters) stays below 1 KB
+    // kernel's static shared memory (descriptor copy, slice starts, counters)
+    // stays below 5 KB
     const size_t per_cta = ds->smem_per_sm / 2;
-    size_t v = per_cta > 2048 ? per_cta - 2048 : 0;
+    size_t v = per_cta > 6144 ? per_cta - 6144 : 0;
     v = std::min(v, ds->smem_optin);
     return (uint32_t)(v & ~(size_t)15);
 }
+
+uint32_t batch_grid(const DeviceState *ds) { return 2u * (uint32_t)ds->sm_count; }
 
 uint32_t batch_scheme(int32_t strategy) {
     switch (strategy) {
@@ -29,6 +32,19 @@ uint32_t batch_scheme(int32_t strategy) {
 }
 
 static uint32_t round16(uint32_t v) { return (v + 15u) & ~15u; }
+
+uint32_t item_quads_for(uint64_t quads, uint32_t scheme, uint32_t grid) {
+    if (scheme == BS_TILE || grid == 0) return kItemQuads;
+    const uint64_t q = (quads + grid - 1) / grid;
+    return (uint32_t)std::min<uint64_t>(kItemQuads, std::max<uint64_t>(kMinItemQuads, q));
+}
+
+void set_strategy(PlannedSlice &ps, int32_t strategy, uint32_t grid) {
+    ps.strategy = strategy;
+    ps.d.strat = batch_scheme(strategy);
+    ps.d.item_quads = item_quads_for(ps.d.r.g.quads, ps.d.strat, grid);
+    ps.items = (uint32_t)((ps.d.r.g.quads + ps.d.item_quads - 1) / ps.d.item_quads);
+}
 
 sinet_status check_slice(const sinet_batch_slice &u) {
     if (!u.table) return SINET_ERR_INVALID_ARG;
@@ -71,10 +87,8 @@ sinet_status plan_slice(const sinet_batch_slice &u, const DeviceState *ds, uint3
     d.tile_bins = (uint32_t)std::min<uint64_t>(T, 0xFFFFFFFFull);
     ps.tile_fits = staged + 16 * T <= smem;
     d.zero = u.params.accumulate ? 0u : 1u;
-    ps.strategy = u.params.strategy;
-    if (ps.strategy == SINET_STRAT_SMEM_FULL && !ps.tile_fits) return SINET_ERR_UNSUPPORTED;
-    d.strat = ps.strategy == SINET_STRAT_AUTO ? BS_AGG : batch_scheme(ps.strategy);
-    ps.items = (uint32_t)((d.r.g.quads + kItemQuads - 1) / kItemQuads);
+    if (u.params.strategy == SINET_STRAT_SMEM_FULL && !ps.tile_fits) return SINET_ERR_UNSUPPORTED;
+    set_strategy(ps, u.params.strategy, batch_grid(ds));  // AUTO: resolved later
     ps.zero_items = d.zero ? (uint32_t)((u.params.n_bins + kZeroBins - 1) / kZeroBins) : 0u;
     return SINET_OK;
 }
@@ -122,7 +136,6 @@ void BatchEngine::image(const std::vector<PlannedSlice> &v, std::vector<uint8_t>
     item[n] = (uint32_t)ti;
     zero[n] = (uint32_t)tz;
     hdr.n_slices = n;
-    hdr.item_quads = kItemQuads;
     hdr.total_items = (uint32_t)ti;
     hdr.total_zero = (uint32_t)tz;
     std::memcpy(buf.data(), &hdr, sizeof hdr);
@@ -246,7 +259,6 @@ sinet_status tune_one(const PlannedSlice &rep, const DeviceState *ds, uint32_t s
     PlannedSlice ps = rep;
     const uint64_t n = std::min<uint64_t>(rep.d.r.g.n, kTuneRecords);
     ps.d.r.g = make_geom(n, {{ps.d.r.ts, 8}, {ps.d.r.src, 4}, {ps.d.r.dst, 4}, {ps.d.r.bytes, 4}});
-    ps.items = (uint32_t)((ps.d.r.g.quads + kItemQuads - 1) / kItemQuads);
     const uint32_t nb = ps.d.h.n_bins;
     uint8_t *m = static_cast<uint8_t *>(scratch);
     ps.d.h.cnt[0] = reinterpret_cast<uint32_t *>(m);
@@ -266,7 +278,7 @@ sinet_status tune_one(const PlannedSlice &rep, const DeviceState *ds, uint32_t s
     std::vector<uint8_t> buf;
     sinet_status st = SINET_OK;
     for (int c = 0; c < nc && st == SINET_OK; ++c) {
-        ps.d.strat = batch_scheme(cands[c]);
+        set_strategy(ps, cands[c], (uint32_t)eng.grid);
         eng.image({ps}, buf);
         cudaError_t e = cudaMemcpyAsync(eng.d_mem, buf.data(), buf.size(), cudaMemcpyHostToDevice, s);
         float ms = 1e30f;
@@ -342,8 +354,7 @@ sinet_status resolve_strategies(std::vector<PlannedSlice> &v, bool tune, const D
         auto it = g_tune.find(keys[i]);
         int32_t s_ = it != g_tune.end() ? it->second : fixed_rule(v[i]);
         if (s_ == SINET_STRAT_SMEM_FULL && !v[i].tile_fits) s_ = fixed_rule(v[i]);
-        v[i].strategy = s_;
-        v[i].d.strat = batch_scheme(s_);
+        set_strategy(v[i], s_, batch_grid(ds));
     }
     return SINET_OK;
 }
@@ -375,20 +386,24 @@ sinet_status sinet_batch_create(const sinet_batch_slice *slices, uint32_t n_slic
     if (st != SINET_OK) return st;
     const uint32_t smem = batch_smem(ds);
     std::vector<PlannedSlice> v(n_slices);
-    uint64_t items = 0, zitems = 0, records = 0;
+    uint64_t records = 0;
     for (uint32_t i = 0; i < n_slices; ++i) {
         if ((st = plan_slice(slices[i], ds, smem, v[i])) != SINET_OK) return st;
         v[i].user_index = i;
-        items += v[i].items;
-        zitems += v[i].zero_items;
         records += slices[i].n;
     }
-    if (items >= 0xFFFFFFFFull || zitems >= 0xFFFFFFFFull) return SINET_ERR_UNSUPPORTED;
     if ((st = resolve_strategies(v, (flags & SINET_BATCH_AUTOTUNE) != 0, ds, smem, stream)) != SINET_OK)
         return st;
+    uint64_t items = 0, zitems = 0;
+    for (const PlannedSlice &ps : v) {
+        items += ps.items;
+        zitems += ps.zero_items;
+    }
+    if (items >= 0xFFFFFFFFull || zitems >= 0xFFFFFFFFull) return SINET_ERR_UNSUPPORTED;
     // largest slices first: the last work items handed out are the small ones
-    std::stable_sort(v.begin(), v.end(),
-                     [](const PlannedSlice &a, const PlannedSlice &b) { return a.items > b.items; });
+    std::stable_sort(v.begin(), v.end(), [](const PlannedSlice &a, const PlannedSlice &b) {
+        return a.d.r.g.quads > b.d.r.g.quads;
+    });
     sinet_batch *b = new (std::nothrow) sinet_batch();
     if (!b) return SINET_ERR_OOM;
     b->strategy.resize(n_slices);

@@ -83,6 +83,17 @@ __device__ __forceinline__ uint32_t ld_stream_u8(const uint8_t *ptr) {
     return v;
 }
 
+// Global-memory reductions (no return value). Written out so that they are
+// always RED.global, also where the compiler cannot tell a pointer is global,
+// and carry no memory clobber: nothing in a kernel reads the histogram back.
+__device__ __forceinline__ void red_add_u32(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v));
+}
+
+__device__ __forceinline__ void red_add_u64(uint64_t *p, uint64_t v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
+
 // ---------------------------------------------------------------------------
 // Bulk (TMA engine, non-tensor) copy of a 16-byte-aligned global region into
 // shared memory, completed on an mbarrier. Called by all threads of the CTA;

@@ -57,13 +57,15 @@ struct BatchSlice {
     uint32_t strat;      // BS_*
     uint32_t tile_bins;  // BS_TILE: bins per direction of the tile (>= n_bins, multiple of 4)
     uint32_t zero;       // 1: the outputs are zeroed by the launch (not accumulated into)
+    uint32_t item_quads; // quads per work item of this slice
+    uint32_t pad;
 };
 
 // Device-resident header read by both batch kernels at every launch, so one
 // captured graph serves any slice set up to its capacity.
 struct BatchHeader {
     uint32_t n_slices;
-    uint32_t item_quads;   // quads per work item
+    uint32_t reserved;
     uint32_t total_items;  // work items of all slices
     uint32_t total_zero;   // zeroing items of all slices
     uint32_t counter;      // work-item counter, reset by the zeroing kernel
@@ -84,7 +86,9 @@ constexpr uint32_t kZeroBins = 1u << 16;
 constexpr uint32_t kBatchCacheSetBits = 9;
 constexpr uint32_t kBatchCacheBytes = 16u << (kBatchCacheSetBits + 2);
 // Threads of a batch CTA.
-constexpr int kBatchBlock = 512;
+constexpr int kBatchBlock = 384;
+// Batches of at most this many slices keep their work-item starts in shared memory.
+constexpr uint32_t kBatchSmemStarts = 1024;
 
 // Zero the outputs of the slices marked `zero` and reset the work counter.
 cudaError_t run_batch_zero(const BatchArgs &b, int grid, cudaStream_t s);

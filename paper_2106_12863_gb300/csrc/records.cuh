@@ -320,8 +320,8 @@ __device__ __forceinline__ void flush_counters(uint64_t *stats, const uint32_t c
 __device__ __forceinline__ void gadd(const HistArgs &h, uint32_t d, uint32_t bin, uint32_t c, uint64_t s) {
     uint32_t *cp = d ? h.cnt[1] : h.cnt[0];
     uint64_t *bp = d ? h.byt[1] : h.byt[0];
-    atomicAdd(cp + bin, c);
-    atomicAdd(reinterpret_cast<unsigned long long *>(bp + bin), (unsigned long long)s);
+    red_add_u32(cp + bin, c);
+    red_add_u64(bp + bin, s);
 }
 
 }  // namespace sinet
