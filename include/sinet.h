@@ -286,10 +286,11 @@ typedef struct sinet_batch sinet_batch;
  * histogram fits a shared-memory tile, log2 of n_bins and of n, unit bin
  * width, both-direction policy); with SINET_BATCH_AUTOTUNE, each class not
  * yet in the process-wide cache is tuned by timing every candidate strategy
- * on its largest slice (its first 8 M records at most, into scratch outputs:
- * the slice's own outputs are not touched), and the fastest is cached and, if
- * the environment variable SINET_AUTOTUNE_CACHE names a file, appended to it
- * (the file is read on first use). Without the flag a class absent from the
+ * on its largest slice (its first 8 M records at most, run as enough copies
+ * to keep every CTA busy, into scratch outputs: the slice's own outputs are
+ * not touched); the fastest per record is cached and, if the environment
+ * variable SINET_AUTOTUNE_CACHE names a file, appended to it as a line
+ * "class strategy ns_per_record" (the file is read on first use). Without the flag a class absent from the
  * cache takes a fixed rule. Tuning runs on `stream` and synchronises it.
  * The records, tables and outputs are referenced, not copied: they must
  * stay valid, and the records unchanged between runs only if the caller

@@ -15,8 +15,10 @@ namespace sinet {
 // histograms under random read-modify-write stay few enough to share L2.
 constexpr uint32_t kItemQuads = 16000;
 constexpr uint32_t kMinItemQuads = 4096;
-// Records a tuning run processes at most per candidate.
+// Records of the representative slice a tuning run uses at most, and the most
+// copies of it one tuning launch runs.
 constexpr uint64_t kTuneRecords = 8ull << 20;
+constexpr uint32_t kTuneCopies = 64;
 
 struct PlannedSlice {
     BatchSlice d;

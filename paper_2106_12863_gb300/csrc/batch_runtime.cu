@@ -234,12 +234,12 @@ void load_cache_file() {
     std::fclose(f);
 }
 
-void append_cache_file(const std::string &key, int32_t s, float ms) {
+void append_cache_file(const std::string &key, int32_t s, float ns_per_record) {
     const char *path = std::getenv("SINET_AUTOTUNE_CACHE");
     if (!path || !*path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %s %.4f\n", key.c_str(), strategy_name(s), ms);
+    std::fprintf(f, "%s %s %.4f\n", key.c_str(), strategy_name(s), ns_per_record);
     std::fclose(f);
 }
 
@@ -253,19 +253,19 @@ int32_t fixed_rule(const PlannedSlice &ps) {
     return SINET_STRAT_ATOMIC_NOAGG;
 }
 
-// Time the candidates on one representative slice; returns the fastest.
+// Time the candidates on one representative slice; returns the fastest per
+// record. A batch keeps every CTA busy, so each candidate runs on enough
+// copies of the slice (its first kTuneRecords records) to give the grid two
+// work items per CTA: timed alone, a slice cut into few large items would
+// leave most of the GPU idle and look slower than it is inside a batch. The
+// copies write separate scratch outputs when those stay small, else share one.
 sinet_status tune_one(const PlannedSlice &rep, const DeviceState *ds, uint32_t smem, cudaStream_t s,
-                      BatchEngine &eng, void *scratch, int32_t *best, float *best_ms) {
+                      BatchEngine &eng, int32_t *best, float *best_ns) {
     PlannedSlice ps = rep;
     const uint64_t n = std::min<uint64_t>(rep.d.r.g.n, kTuneRecords);
     ps.d.r.g = make_geom(n, {{ps.d.r.ts, 8}, {ps.d.r.src, 4}, {ps.d.r.dst, 4}, {ps.d.r.bytes, 4}});
     const uint32_t nb = ps.d.h.n_bins;
-    uint8_t *m = static_cast<uint8_t *>(scratch);
-    ps.d.h.cnt[0] = reinterpret_cast<uint32_t *>(m);
-    ps.d.h.cnt[1] = ps.d.h.cnt[0] + nb;
-    ps.d.h.byt[0] = reinterpret_cast<uint64_t *>(m + (((size_t)8 * nb + 15) & ~(size_t)15));
-    ps.d.h.byt[1] = ps.d.h.byt[0] + nb;
-    ps.d.h.stats = ps.d.h.byt[1] + nb;
+    const size_t out_bytes = (((size_t)8 * nb + 15) & ~(size_t)15) + (size_t)16 * nb + 64;
     ps.d.zero = 1;
     ps.zero_items = (nb + kZeroBins - 1) / kZeroBins;
     int32_t cands[3] = {SINET_STRAT_GLOBAL_ATOMIC, SINET_STRAT_ATOMIC_NOAGG, SINET_STRAT_SMEM_FULL};
@@ -274,13 +274,32 @@ sinet_status tune_one(const PlannedSlice &rep, const DeviceState *ds, uint32_t s
     SINET_CUDA(cudaEventCreate(&e0));
     SINET_CUDA(cudaEventCreate(&e1));
     *best = -1;
-    *best_ms = 0.f;
+    *best_ns = 0.f;
     std::vector<uint8_t> buf;
     sinet_status st = SINET_OK;
     for (int c = 0; c < nc && st == SINET_OK; ++c) {
         set_strategy(ps, cands[c], (uint32_t)eng.grid);
-        eng.image({ps}, buf);
-        cudaError_t e = cudaMemcpyAsync(eng.d_mem, buf.data(), buf.size(), cudaMemcpyHostToDevice, s);
+        uint32_t copies = ps.items ? (uint32_t)((2ull * eng.grid + ps.items - 1) / ps.items) : 1u;
+        copies = std::max<uint32_t>(1, std::min<uint32_t>({copies, eng.cap,
+                                                           (uint32_t)std::max<uint64_t>(1, (4 * kTuneRecords) / std::max<uint64_t>(n, 1))}));
+        const bool separate = (size_t)copies * out_bytes <= (512ull << 20);
+        void *scratch = nullptr;
+        cudaError_t e = cudaMalloc(&scratch, separate ? copies * out_bytes : out_bytes);
+        std::vector<PlannedSlice> v(copies, ps);
+        for (uint32_t k = 0; k < copies && e == cudaSuccess; ++k) {
+            uint8_t *m = static_cast<uint8_t *>(scratch) + (separate ? k * out_bytes : 0);
+            HistArgs &h = v[k].d.h;
+            h.cnt[0] = reinterpret_cast<uint32_t *>(m);
+            h.cnt[1] = h.cnt[0] + nb;
+            h.byt[0] = reinterpret_cast<uint64_t *>(m + (((size_t)8 * nb + 15) & ~(size_t)15));
+            h.byt[1] = h.byt[0] + nb;
+            h.stats = h.byt[1] + nb;
+            if (!separate && k) v[k].zero_items = 0;  // zeroed once
+        }
+        if (e == cudaSuccess) {
+            eng.image(v, buf);
+            e = cudaMemcpyAsync(eng.d_mem, buf.data(), buf.size(), cudaMemcpyHostToDevice, s);
+        }
         float ms = 1e30f;
         for (int rep_i = 0; rep_i < 4 && e == cudaSuccess; ++rep_i) {
             e = cudaEventRecord(e0, s);
@@ -292,13 +311,18 @@ sinet_status tune_one(const PlannedSlice &rep, const DeviceState *ds, uint32_t s
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
             if (e == cudaSuccess && rep_i > 0) ms = std::min(ms, t);  // the first run warms up
         }
+        if (scratch) {
+            const cudaError_t e2 = cudaFree(scratch);
+            if (e == cudaSuccess) e = e2;
+        }
         if (e != cudaSuccess) {
             st = cuda_fail(e);
             break;
         }
-        if (*best < 0 || ms < *best_ms) {
+        const float ns = ms * 1e6f / (float)((double)copies * (double)std::max<uint64_t>(n, 1));
+        if (*best < 0 || ns < *best_ns) {
             *best = cands[c];
-            *best_ms = ms;
+            *best_ns = ns;
         }
     }
     cudaEventDestroy(e0);
@@ -322,29 +346,22 @@ sinet_status resolve_strategies(std::vector<PlannedSlice> &v, bool tune, const D
         if (it == rep.end() || v[i].d.r.g.n > v[it->second].d.r.g.n) rep[keys[i]] = i;
     }
     if (tune) {
-        uint64_t max_bins = 0;
-        for (auto &kv : rep)
-            if (!g_tune.count(kv.first)) max_bins = std::max<uint64_t>(max_bins, v[kv.second].d.h.n_bins);
-        if (max_bins) {
+        bool any = false;
+        for (auto &kv : rep) any = any || !g_tune.count(kv.first);
+        if (any) {
             BatchEngine eng;
-            void *scratch = nullptr;
-            sinet_status st = eng.init(1, ds, smem);
-            if (st == SINET_OK) {
-                cudaError_t e = cudaMalloc(&scratch, 24 * max_bins + 256);
-                if (e != cudaSuccess) st = cuda_fail(e);
-            }
+            sinet_status st = eng.init(kTuneCopies, ds, smem);
             for (auto &kv : rep) {
                 if (st != SINET_OK) break;
                 if (g_tune.count(kv.first)) continue;
                 int32_t best = -1;
-                float ms = 0.f;
-                st = tune_one(v[kv.second], ds, smem, s, eng, scratch, &best, &ms);
+                float ns = 0.f;
+                st = tune_one(v[kv.second], ds, smem, s, eng, &best, &ns);
                 if (st == SINET_OK && best >= 0) {
                     g_tune[kv.first] = best;
-                    append_cache_file(kv.first, best, ms);
+                    append_cache_file(kv.first, best, ns);
                 }
             }
-            if (scratch) cudaFree(scratch);
             eng.release();
             if (st != SINET_OK) return st;
         }
