@@ -45,10 +45,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="day", choices=sorted(gen.WORKLOADS) + ["batch"],
+    ap.add_argument("--workload", default="day", choices=sorted(gen.WORKLOADS) + ["batch", "serve"],
                     help="day | heavy | tiny: one window; batch: 256 uneven slices in one "
-                         "persistent launch")
+                         "persistent launch; serve: the continuous-batching serving loop")
     ap.add_argument("--slices", type=int, default=256, help="batch: number of slices")
+    ap.add_argument("--tenants", type=int, default=32, help="serve: tenants")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests per phase")
+    ap.add_argument("--request-cap", type=int, default=16_000_000,
+                    help="serve: largest request (records); sizes above it are capped")
+    ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: in-flight arena")
     ap.add_argument("--records", type=int, default=0, help="override the record count")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink records, window and bins together (keeps records per bin; "
@@ -218,7 +223,7 @@ def run_reference(args):
     import oracle
 
     o = oracle.get()
-    if args.workload == "batch":
+    if args.workload in ("batch", "serve"):
         run_reference_batch(args, o)
         return
     w = workload(args, rank)
@@ -465,25 +470,36 @@ def run_batch_bench(args):
 
 
 def run_reference_batch(args, o):
-    """The oracle on the batch workload: step s runs slice s (cyclically), on
-    a prefix sized so all steps fit about 2.5 minutes."""
-    plan = gen.batch_slices(n_slices=args.slices)
+    """The oracle on the batch (or serving) workload: step s runs slice (or
+    request) s, cyclically, on a prefix sized so all steps fit about 2.5
+    minutes."""
+    if args.workload == "serve":
+        specs, reqs = gen.serving_plan(n_tenants=args.tenants, n_requests=args.requests,
+                                       cap=args.request_cap)
+        items = [(specs[r.tenant], gen.BASE_SEED + 5000 + r.tenant, r.records, r.seed, r.n, 0, 1,
+                  gen.DAY_MS) for r in reqs]
+        name = f"serve-{len(specs)}-tenants-lognormal-1M"
+    else:
+        plan = gen.batch_slices(n_slices=args.slices)
+        items = [(sp.table, sp.seed, sp.records, sp.seed, sp.n, sp.t0, sp.bin_width, sp.n_bins)
+                 for sp in plan]
+        name = f"batch-{len(plan)}-slices-uneven"
     per_step = max(0.05, 150.0 / (args.steps + args.warmup))
-    sp = plan[0]
-    net, ln = gen.make_table(sp.table, sp.seed)
-    probe = min(50_000, sp.n)
-    rec = gen.make_records(sp.records, sp.seed, net, ln, n=probe)
+    tspec, tseed, rspec, rseed, n0, t0, w, nb = items[0]
+    net, ln = gen.make_table(tspec, tseed)
+    probe = min(50_000, n0)
+    rec = gen.make_records(rspec, rseed, net, ln, n=probe)
     t = time.perf_counter()
-    o.discriminate_histogram(net, ln, rec, sp.t0, sp.bin_width, sp.n_bins)
+    o.discriminate_histogram(net, ln, rec, t0, w, nb)
     rate = probe / max(time.perf_counter() - t, 1e-6)
     done, total = 0, 0.0
     for s in range(args.warmup + args.steps):
-        sp = plan[s % len(plan)]
-        net, ln = gen.make_table(sp.table, sp.seed)
-        m = max(1, min(sp.n, int(rate * per_step)))
-        rec = gen.make_records(sp.records, sp.seed, net, ln, n=m)
+        tspec, tseed, rspec, rseed, n_s, t0, w, nb = items[s % len(items)]
+        net, ln = gen.make_table(tspec, tseed)
+        m = max(1, min(n_s, int(rate * per_step)))
+        rec = gen.make_records(rspec, rseed, net, ln, n=m)
         t = time.perf_counter()
-        o.discriminate_histogram(net, ln, rec, sp.t0, sp.bin_width, sp.n_bins)
+        o.discriminate_histogram(net, ln, rec, t0, w, nb)
         dt = time.perf_counter() - t
         if s >= args.warmup:
             done += m
@@ -493,11 +509,154 @@ def run_reference_batch(args, o):
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"batch-{len(plan)}-slices-uneven", "records_per_step": done // args.steps},
+            "config": {"workload": name, "records_per_step": done // args.steps},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
-                             "sample": "a prefix of one slice per step, slices taken in order"},
+                             "sample": "a prefix of one slice (request) per step, taken in order"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_serve_bench(args):
+    """The serving loop: tenants with resident day histograms; request sizes
+    log-normal (median 1 M records, p99 50 M before the cap), each uniform over
+    a random window of its tenant's day. Saturated throughput first (all
+    requests queued at once), then Poisson arrivals at 50% and 80% of it."""
+    from dataclasses import replace
+
+    rank, world, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2106_12863_gb300 as sinet
+
+    sinet.load()
+    specs, reqs = gen.serving_plan(n_tenants=args.tenants, n_requests=3 * args.requests,
+                                   seed=gen.BASE_SEED + 5 + 1000 * rank, cap=args.request_cap)
+    tg = time.perf_counter()
+    tables, pools = [], []
+    cap = max(r.n for r in reqs)
+    for i, sp in enumerate(specs):
+        net, ln = gen.make_table(sp, gen.BASE_SEED + 5000 + i)
+        tables.append(sinet.PrefixTable(net, ln))
+    # one pinned pool of records per tenant; a request of n records for
+    # tenant t is the first n records of a window-shaped stream of t's pool
+    for i, sp in enumerate(specs):
+        net, ln = gen.make_table(sp, gen.BASE_SEED + 5000 + i)
+        n_i = max([r.n for r in reqs if r.tenant == i] + [1])
+        pool = {"ts": torch.empty(n_i, dtype=torch.int64, pin_memory=True),
+                "src": torch.empty(n_i, dtype=torch.int32, pin_memory=True),
+                "dst": torch.empty(n_i, dtype=torch.int32, pin_memory=True),
+                "bytes": torch.empty(n_i, dtype=torch.int32, pin_memory=True)}
+        first = next((r for r in reqs if r.tenant == i), None)
+        rs = first.records if first else gen.RecordSpec(n_i)
+        gen.fill_records(replace(rs, n=n_i), gen.BASE_SEED + 6000 + i, net, ln, 0, n_i,
+                         pool["ts"], pool["src"], pool["dst"], pool["bytes"])
+        pools.append(pool)
+    t_gen = time.perf_counter() - tg
+    params = [sinet.HistParams(0, 1, gen.DAY_MS, accumulate=True) for _ in specs]
+    server = sinet.Server(list(zip(tables, params)), budget_bytes=int(args.budget_gb * (1 << 30)),
+                          max_requests_per_launch=256)
+
+    def submit(r):
+        p = pools[r.tenant]
+        return server.submit(r.tenant, p["ts"][:r.n], p["src"][:r.n], p["dst"][:r.n], p["bytes"][:r.n])
+
+    phase = [reqs[k * args.requests:(k + 1) * args.requests] for k in range(3)]
+    # warm-up
+    for k in [submit(r) for r in phase[0][:max(3, args.warmup)]]:
+        server.wait(k)
+    server.drain()
+    server.stats(reset=True)
+    # saturated: everything queued at once
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    clocks.mark(True)
+    t0 = time.perf_counter()
+    ks = [submit(r) for r in phase[0]]
+    server.drain()
+    t_sat = time.perf_counter() - t0
+    clocks.mark(False)
+    clk = clocks.stop()
+    for k in ks:
+        server.wait(k)
+    st = server.stats(reset=True)
+    n_sat = sum(r.n for r in phase[0])
+    sat = n_sat / t_sat
+    serving = {"saturated": {"records_per_s": sat, "requests": len(phase[0]), "launches": st["launches"],
+                             "p50_ms": st["p50_latency_ns"] / 1e6, "p99_ms": st["p99_latency_ns"] / 1e6,
+                             "gpu_busy_frac": st["busy_ns"] / 1e9 / t_sat}}
+    mean_n = n_sat / len(phase[0])
+    for rho, ph in ((0.5, phase[1]), (0.8, phase[2])):
+        lam = rho * sat / mean_n  # requests per second
+        ks, t_next = [], time.perf_counter()
+        t_start = t_next
+        for r in ph:
+            t_next += r.gap / lam
+            while time.perf_counter() < t_next:
+                pass
+            ks.append(submit(r))
+        server.drain()
+        t_el = time.perf_counter() - t_start
+        for k in ks:
+            server.wait(k)
+        st = server.stats(reset=True)
+        serving[f"rho_{rho}"] = {"offered_records_per_s": rho * sat,
+                                 "achieved_records_per_s": sum(r.n for r in ph) / t_el,
+                                 "requests": len(ph), "launches": st["launches"],
+                                 "p50_ms": st["p50_latency_ns"] / 1e6, "p99_ms": st["p99_latency_ns"] / 1e6,
+                                 "max_ms": st["max_latency_ns"] / 1e6}
+    h2d = RECORD_BYTES * mean_n
+    result = {"metric": METRIC, "value": world * sat, "unit": UNIT, "n_gpus": world,
+              "steps": len(phase[0]), "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_sat / len(phase[0]),
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+              "data": "synthetic (seeded generator; Poisson request stream)"}
+    peak, peak_kind = peaks()
+    achieved = RECORD_BYTES * sat / 1e9
+    result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "traffic": None, "kernel": "k_batch (serving launches)",
+                          "peak_kind": peak_kind,
+                          "note": "record bytes only, end to end: every record also crosses host-to-device"}
+    result["gpu_launches"] = serving["saturated"]["launches"]
+    result["e2e"] = {"value": world * sat, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                     "d2h_bytes_per_step": 0, "step": "one request (results stay resident)"}
+    result["config"] = {"workload": f"serve-{len(specs)}-tenants-lognormal-1M", "tenants": len(specs),
+                        "n_bins_per_tenant": gen.DAY_MS, "resident_gb": 24 * gen.DAY_MS * len(specs) / 1e9,
+                        "inflight_budget_gb": args.budget_gb, "request_cap": args.request_cap,
+                        "mean_request_records": mean_n, "policy": "exclusive",
+                        "parallelism": f"replicas x{world} (weak)", "gen_s": round(t_gen, 1),
+                        "l2": "inputs larger than L2"}
+    result["serving"] = serving
+    result["clocks"] = clk
+    if rank == 0 and not args.no_cpu:
+        import oracle
+
+        o_ = oracle.get()
+        done, t_cpu, i = 0, 0.0, 0
+        while t_cpu < args.cpu_seconds and i < len(phase[0]):
+            r = phase[0][i]
+            net, ln = gen.make_table(specs[r.tenant], gen.BASE_SEED + 5000 + r.tenant)
+            m = min(r.n, 2_000_000)
+            p = pools[r.tenant]
+            rec = {"ts": p["ts"][:m].numpy().view(np.uint64), "src": p["src"][:m].numpy().view(np.uint32),
+                   "dst": p["dst"][:m].numpy().view(np.uint32), "bytes": p["bytes"][:m].numpy().view(np.uint32)}
+            t0_ = time.perf_counter()
+            o_.discriminate_histogram(net, ln, rec, 0, 1, gen.DAY_MS)
+            t_cpu += time.perf_counter() - t0_
+            done += m
+            i += 1
+        result["cpu_baseline"] = {"value": done / t_cpu, "unit": UNIT, "cores": o_.threads(), "kind": "oracle",
+                                  "sample": f"{i} requests (at most 2 M records each, {done} records), "
+                                            f"one oracle call each into a day histogram; {t_cpu:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    server.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def main():
@@ -507,6 +666,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch_bench(args)
+        return
+    if args.workload == "serve":
+        run_serve_bench(args)
         return
     rank, world, local = dist_env()
     import torch

@@ -271,3 +271,43 @@ def batch_slices(n_slices: int = 256, seed: int = BASE_SEED + 4, n_lo: int = 10_
         rspec = RecordSpec(n, ts_kind="uniform", t_lo=t0, t_hi=t0 + window)
         out.append(SliceSpec(i, n, t0, window, w, n_bins, tspec, seed * 1000 + i, rspec))
     return out
+
+
+# --------------------------------------------------------------------------
+# Serving stream (tenants with their own tables; Poisson arrivals; log-normal
+# request sizes; each request uniform over a random window of its tenant's day)
+
+
+@dataclass
+class RequestSpec:
+    index: int
+    tenant: int
+    n: int
+    gap: float  # exponential(1) inter-arrival gap, scaled by 1 / rate by the caller
+    seed: int
+    records: RecordSpec
+
+
+def serving_plan(n_tenants: int = 32, n_requests: int = 1000, seed: int = BASE_SEED + 5,
+                 median: float = 1_000_000, sigma: float = math.log(50) / 2.326,
+                 cap: int | None = None, p_lo: int = 500, p_hi: int = 4000):
+    """(tenant table specs, request specs). Request sizes are log-normal with the
+    given median and sigma (p99 = 50 x median by default), capped at ``cap``;
+    windows are log-uniform 1 min - 6 h at a uniform start within the day."""
+    t = u64_stream(seed, 1, n_tenants)
+    tables = [TableSpec(p_lo + int((int(x) >> 11) * 2.0 ** -53 * (p_hi - p_lo + 1)), 8, 32) for x in t]
+    r = u64_stream(seed, 2, 6 * n_requests).reshape(n_requests, 6)
+    u = ((r >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    out = []
+    for i in range(n_requests):
+        z = math.sqrt(-2.0 * math.log(u[i, 0])) * math.cos(2.0 * math.pi * u[i, 1])  # Box-Muller
+        n = max(1, int(median * math.exp(sigma * z)))
+        if cap:
+            n = min(n, cap)
+        tenant = min(int(u[i, 2] * n_tenants), n_tenants - 1)
+        window = int(math.exp(math.log(60_000) + u[i, 3] * (math.log(21_600_000) - math.log(60_000))))
+        t_lo = int(u[i, 4] * (DAY_MS - window))
+        gap = -math.log(u[i, 5])
+        out.append(RequestSpec(i, tenant, n, gap, seed * 1000 + i,
+                               RecordSpec(n, ts_kind="uniform", t_lo=t_lo, t_hi=t_lo + window)))
+    return tables, out

@@ -316,6 +316,94 @@ sinet_status sinet_batch_info(const sinet_batch *b, uint64_t *work_items, uint64
 /* Synchronise the device, then free the batch (NULL is a no-op). */
 sinet_status sinet_batch_destroy(sinet_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Serving loop with continuous batching (Section 4's bounded work queue:
+ * chunks are queued by a producer and each is to be processed within a
+ * bounded time).
+ *
+ * A server owns, for each tenant, a prefix table reference, histogram
+ * parameters and a RESIDENT histogram in device memory that every request of
+ * the tenant accumulates into. Requests carry host records. A worker thread
+ * admits queued requests in arrival order while the in-flight budget (a
+ * device arena holding the admitted requests' records) has room, copies their
+ * records to the device on a copy stream while the previous launch runs, and
+ * then starts one batched launch (the kernel of sinet_batch_run) over every
+ * admitted request whose copy has been issued, up to max_requests_per_launch.
+ * A request is done when its launch has completed; its arena space is then
+ * reused.
+ */
+typedef struct {
+    const sinet_prefix_table *table; /* must outlive the server */
+    sinet_hist_params params;        /* window, width, bins, policy; strategy AUTO, GLOBAL_ATOMIC,
+                                        ATOMIC_NOAGG or SMEM_FULL; accumulate is implied */
+} sinet_tenant;
+
+typedef struct {
+    uint64_t inflight_budget_bytes;   /* device arena for admitted requests' records (>= 1 MiB) */
+    uint32_t max_requests_per_launch; /* requests one launch takes, 1..4096 */
+    uint32_t max_queued;              /* submitted, not yet done requests; beyond it submit
+                                         returns SINET_ERR_BUDGET */
+} sinet_server_config;
+
+typedef struct {
+    uint64_t n;          /* records */
+    uint64_t launch;     /* sequence number of the launch that processed it */
+    uint64_t latency_ns; /* from submit to the host seeing its launch complete */
+} sinet_request_info;
+
+typedef struct {
+    uint64_t requests_done;
+    uint64_t records_done;
+    uint64_t launches;
+    uint64_t p50_latency_ns; /* over requests done since the last reset */
+    uint64_t p99_latency_ns;
+    uint64_t max_latency_ns;
+    uint64_t busy_ns;        /* host-observed time with a launch in flight */
+} sinet_server_counters;
+
+typedef struct sinet_server sinet_server;
+
+/* Create a server on the current device: allocates the tenants' resident
+ * histograms (zeroed; 24 bytes per bin) and the arena, captures the launch,
+ * and starts the worker. SINET_ERR_INVALID_ARG for bad tenants or config
+ * (checked as in sinet_batch_create), SINET_ERR_OOM if device memory runs out. */
+sinet_status sinet_server_create(const sinet_server_config *cfg, const sinet_tenant *tenants,
+                                 uint32_t n_tenants, sinet_server **out);
+
+/* Queue a request of n records (host pointers, each aligned to its element
+ * size; pinned memory lets the copy overlap). The buffers must stay valid and
+ * unchanged until the request is done. Returns SINET_ERR_BUDGET, queueing
+ * nothing, if 20 n bytes (plus alignment) exceed the whole arena or
+ * max_queued requests are outstanding; *ticket identifies the request. */
+sinet_status sinet_server_submit(sinet_server *s, uint32_t tenant, const uint64_t *h_ts,
+                                 const uint32_t *h_src, const uint32_t *h_dst, const uint32_t *h_bytes,
+                                 uint64_t n, uint64_t *ticket);
+
+/* Block until the request is done (info may be NULL), or return
+ * SINET_ERR_TIMEOUT after timeout_ms. A done request's info can be read once;
+ * SINET_ERR_INVALID_ARG for an unknown or already collected ticket. */
+sinet_status sinet_server_wait(sinet_server *s, uint64_t ticket, uint32_t timeout_ms,
+                               sinet_request_info *info);
+
+/* Block until every submitted request is done, or SINET_ERR_TIMEOUT. */
+sinet_status sinet_server_drain(sinet_server *s, uint32_t timeout_ms);
+
+/* Device pointers of a tenant's resident histogram (read them after a drain). */
+sinet_status sinet_server_tenant_output(sinet_server *s, uint32_t tenant, sinet_hist_out *out);
+
+/* Copy a tenant's resident histogram to host memory (count: uint32[2 * n_bins],
+ * direction 0 first; bytes: uint64[2 * n_bins]; stats: uint64[8]). Waits for
+ * the launch in flight, if any, and for nothing else: drain first for a
+ * result that includes every submitted request. */
+sinet_status sinet_server_export(sinet_server *s, uint32_t tenant, uint32_t *h_count, uint64_t *h_bytes,
+                                 uint64_t *h_stats);
+
+/* Counters and latency percentiles; reset = 1 clears them afterwards. */
+sinet_status sinet_server_stats(sinet_server *s, int reset, sinet_server_counters *st);
+
+/* Stop the worker (requests not yet done are dropped), free everything. */
+sinet_status sinet_server_destroy(sinet_server *s);
+
 /*
  * Read and clear the device status word of the current device, after
  * synchronising `stream`. *device_code receives the latched sinet_status

@@ -65,6 +65,26 @@ class BatchSliceC(ctypes.Structure):
 
 BATCH_AUTOTUNE = 1
 
+
+class TenantC(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_void_p), ("params", HistParamsC)]
+
+
+class ServerConfigC(ctypes.Structure):
+    _fields_ = [("inflight_budget_bytes", ctypes.c_uint64), ("max_requests_per_launch", ctypes.c_uint32),
+                ("max_queued", ctypes.c_uint32)]
+
+
+class RequestInfoC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("launch", ctypes.c_uint64), ("latency_ns", ctypes.c_uint64)]
+
+
+class ServerCountersC(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_uint64), ("records_done", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("p50_latency_ns", ctypes.c_uint64),
+                ("p99_latency_ns", ctypes.c_uint64), ("max_latency_ns", ctypes.c_uint64),
+                ("busy_ns", ctypes.c_uint64)]
+
 _lib = None
 _P = ctypes.c_void_p
 
@@ -102,6 +122,14 @@ def load():
         "sinet_batch_strategy": (ctypes.c_int, [_P, u32, _P]),
         "sinet_batch_info": (ctypes.c_int, [_P, _P, _P]),
         "sinet_batch_destroy": (ctypes.c_int, [_P]),
+        "sinet_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfigC), ctypes.POINTER(TenantC), u32, _P]),
+        "sinet_server_submit": (ctypes.c_int, [_P, u32, _P, _P, _P, _P, u64, _P]),
+        "sinet_server_wait": (ctypes.c_int, [_P, u64, u32, _P]),
+        "sinet_server_drain": (ctypes.c_int, [_P, u32]),
+        "sinet_server_tenant_output": (ctypes.c_int, [_P, u32, ctypes.POINTER(HistOutC)]),
+        "sinet_server_export": (ctypes.c_int, [_P, u32, _P, _P, _P]),
+        "sinet_server_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ServerCountersC)]),
+        "sinet_server_destroy": (ctypes.c_int, [_P]),
         "sinet_default_params": (None, [ctypes.POINTER(HistParamsC), u64, u64, u64]),
     }
     for name, (res, args) in sig.items():
@@ -414,6 +442,86 @@ class Batch:
         if getattr(self, "handle", None):
             sinet_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _hptr(a) -> int | None:
+    """Host address of a numpy array or CPU tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a contiguous array")
+        return a.ctypes.data
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("expected a contiguous CPU tensor")
+    return a.data_ptr()
+
+
+class Server:
+    """Continuous-batching serving loop (C ABI sinet_server_*).
+
+    ``tenants``: sequence of (PrefixTable, HistParams); each tenant keeps a
+    resident histogram that its requests accumulate into. Host record
+    buffers of a request are kept alive here until it is waited for."""
+
+    def __init__(self, tenants, budget_bytes: int = 1 << 30, max_requests_per_launch: int = 256,
+                 max_queued: int = 1 << 20):
+        self._tables = [t for t, _ in tenants]
+        self.n_bins = [p.n_bins for _, p in tenants]
+        arr = (TenantC * len(tenants))()
+        for i, (t, p) in enumerate(tenants):
+            arr[i].table = t.handle
+            arr[i].params = p.c()
+        cfg = ServerConfigC(budget_bytes, max_requests_per_launch, max_queued)
+        h = ctypes.c_void_p()
+        _check(load().sinet_server_create(ctypes.byref(cfg), arr, len(tenants), ctypes.byref(h)),
+               "sinet_server_create")
+        self.handle = int(h.value)
+        self._keep = {}
+
+    def submit(self, tenant: int, ts, src, dst, nbytes) -> int:
+        t = ctypes.c_uint64()
+        n = len(ts)
+        _check(load().sinet_server_submit(self.handle, tenant, _hptr(ts), _hptr(src), _hptr(dst),
+                                          _hptr(nbytes), n, ctypes.byref(t)), "sinet_server_submit")
+        self._keep[int(t.value)] = (ts, src, dst, nbytes)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 120_000) -> dict:
+        info = RequestInfoC()
+        _check(load().sinet_server_wait(self.handle, ticket, timeout_ms, ctypes.byref(info)),
+               "sinet_server_wait")
+        self._keep.pop(ticket, None)
+        return {"n": int(info.n), "launch": int(info.launch), "latency_ns": int(info.latency_ns)}
+
+    def drain(self, timeout_ms: int = 600_000):
+        _check(load().sinet_server_drain(self.handle, timeout_ms), "sinet_server_drain")
+
+    def export(self, tenant: int) -> dict:
+        nb = self.n_bins[tenant]
+        c = np.zeros((2, nb), np.uint32)
+        b = np.zeros((2, nb), np.uint64)
+        st = np.zeros(8, np.uint64)
+        _check(load().sinet_server_export(self.handle, tenant, c.ctypes.data, b.ctypes.data,
+                                          st.ctypes.data), "sinet_server_export")
+        return {"count": c, "bytes": b, "stats": st}
+
+    def stats(self, reset: bool = False) -> dict:
+        c = ServerCountersC()
+        _check(load().sinet_server_stats(self.handle, int(reset), ctypes.byref(c)), "sinet_server_stats")
+        return {k: int(getattr(c, k)) for k, _ in ServerCountersC._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().sinet_server_destroy(self.handle), "sinet_server_destroy")
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:

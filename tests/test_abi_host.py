@@ -221,6 +221,30 @@ def test_batch_validation_rejects_before_any_cuda_call():
     assert L.sinet_batch_destroy(None) == 0
 
 
+def test_server_validation_rejects_before_any_cuda_call():
+    L = sinet.load()
+    h = ctypes.c_void_p()
+    ten = (sinet.TenantC * 1)()
+    ten[0].table = 0x1000
+    ten[0].params = sinet.HistParams(0, 1, 10).c()
+    good = sinet.ServerConfigC(1 << 20, 16, 100)
+    for cfg in (sinet.ServerConfigC(1 << 19, 16, 100), sinet.ServerConfigC(1 << 20, 0, 100),
+                sinet.ServerConfigC(1 << 20, 5000, 100), sinet.ServerConfigC(1 << 20, 16, 0)):
+        assert L.sinet_server_create(ctypes.byref(cfg), ten, 1, ctypes.byref(h)) == 1
+    assert L.sinet_server_create(ctypes.byref(good), ten, 0, ctypes.byref(h)) == 1
+    bad = (sinet.TenantC * 1)()
+    bad[0].params = sinet.HistParams(0, 1, 10).c()  # no table
+    assert L.sinet_server_create(ctypes.byref(good), bad, 1, ctypes.byref(h)) == 1
+    bad[0].table = 0x1000
+    bad[0].params = sinet.HistParams(0, 0, 10).c()  # zero bin width
+    assert L.sinet_server_create(ctypes.byref(good), bad, 1, ctypes.byref(h)) == 1
+    t = ctypes.c_uint64()
+    assert L.sinet_server_submit(None, 0, None, None, None, None, 0, ctypes.byref(t)) == 1
+    assert L.sinet_server_wait(None, 1, 0, None) == 1
+    assert L.sinet_server_drain(None, 0) == 1
+    assert L.sinet_server_destroy(None) == 0
+
+
 def _toggle_lookup(img, lay, addrs):
     """The shared-memory toggle lookup of the kernels, replayed on the host."""
     desc = img[lay["off_desc"]: lay["off_desc"] + 4 * (1 << lay["desc_bits"])].view(np.uint32)
