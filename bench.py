@@ -292,7 +292,8 @@ def run_batch_bench(args):
     import paper_2106_12863_gb300 as sinet
 
     sinet.load()
-    plan = gen.batch_slices(n_slices=args.slices, seed=gen.BASE_SEED + 4 + 1000 * rank)
+    plan = gen.batch_slices(n_slices=args.slices, seed=gen.BASE_SEED + 4 + 1000 * rank,
+                            scale=args.scale)
     n_tot = sum(sp.n for sp in plan)
     bins_tot = sum(sp.n_bins for sp in plan)
     tg = time.perf_counter()
@@ -380,7 +381,8 @@ def run_batch_bench(args):
                           "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
                           "kernel_ms": graph_ms}
     result["gpu_launches"] = 2 * args.steps  # zeroing kernel + batch kernel per graph replay
-    result["config"] = {"workload": f"batch-{len(plan)}-slices-uneven", "records": n_tot,
+    name = f"batch-{len(plan)}-slices-uneven" + (f"-scale{args.scale:g}" if args.scale != 1.0 else "")
+    result["config"] = {"workload": name, "records": n_tot,
                         "slices": len(plan), "bins_total": bins_tot, "work_items": items,
                         "strategies": strat_count, "tune_s": round(t_tune, 2),
                         "l2": f"inputs larger than L2 ({RECORD_BYTES * n_tot / 1e9:.1f} GB of records)",
