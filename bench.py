@@ -59,7 +59,7 @@ def parse():
                     help="shrink records, window and bins together (keeps records per bin; "
                          "for profiling captures)")
     ap.add_argument("--strategy", default="tune",
-                    help="tune | global_atomic | priv_tile | atomic_noagg | sort_reduce")
+                    help="tune | global_atomic | priv_tile | atomic_noagg | atomic_cell | sort_reduce")
     ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true")
@@ -713,7 +713,8 @@ def main():
         out.stats.zero_()
 
     def writes_every_bin(strategy):
-        return False
+        # the cell strategy expands every bin into the outputs itself
+        return strategy == "atomic_cell"
 
     def step(strategy):
         if writes_every_bin(strategy):
@@ -725,7 +726,7 @@ def main():
                                      params(strategy), out)
 
     # autotune: one untimed run of each candidate, keep the fastest
-    cands = (["priv_tile", "global_atomic", "atomic_noagg"] if args.strategy == "tune"
+    cands = (["priv_tile", "global_atomic", "atomic_noagg", "atomic_cell"] if args.strategy == "tune"
              else [args.strategy])
     tune = {}
     for c in cands:
@@ -790,7 +791,8 @@ def main():
     alg_bytes = RECORD_BYTES * n + BIN_BYTES * w.n_bins
     peak, peak_kind = peaks()
     kname = {"priv_tile": "k_fused_tile", "global_atomic": "k_fused_atomic",
-             "atomic_noagg": "k_fused_atomic", "sort_reduce": "k_radix_pass"}[strategy]
+             "atomic_noagg": "k_fused_atomic", "atomic_cell": "k_fused_atomic",
+             "sort_reduce": "k_radix_pass"}[strategy]
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                           "frac": achieved / peak, "traffic": recorded_traffic(kname, w.name),
@@ -798,8 +800,9 @@ def main():
                           "algorithmic_bytes_per_launch": alg_bytes,
                           "kernel_ms": kern_ms, "zero_ms": zero_ms,
                           "step_frac": alg_bytes / (ms_per_step / 1e3) / 1e9 / peak}
-    # one fused kernel per step (the zeroing is cudaMemsetAsync)
-    result["gpu_launches"] = args.steps
+    # one fused kernel per step (zeroing is cudaMemsetAsync), plus the cell
+    # expansion kernel for the cell strategy
+    result["gpu_launches"] = args.steps * (2 if strategy == "atomic_cell" else 1)
     result["config"] = {"workload": w.name, "records": n, "prefixes": w.table.n,
                         "n_bins": w.n_bins, "bin_width_ms": w.bin_width, "strategy": strategy,
                         "tune_ms": tune, "l2": f"inputs larger than L2 ({RECORD_BYTES * n / 1e9:.1f} GB of records)",

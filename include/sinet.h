@@ -65,7 +65,11 @@ typedef enum {
     SINET_STRAT_PRIV_TILE = 2,     /* shared-memory bin tile per chunk (time-sorted input) */
     SINET_STRAT_SORT_REDUCE = 3,   /* plain path: discriminate, radix sort, reduce by key */
     SINET_STRAT_SMEM_FULL = 4,     /* whole histogram privatised in shared memory (small n_bins) */
-    SINET_STRAT_ATOMIC_NOAGG = 5   /* global atomics without warp aggregation */
+    SINET_STRAT_ATOMIC_NOAGG = 5,  /* global atomics without warp aggregation */
+    SINET_STRAT_ATOMIC_CELL = 6    /* GLOBAL_ATOMIC into a library scratch of one 32-byte cell per
+                                      bin (both directions' count and byte sum in one DRAM sector),
+                                      then expanded into the output arrays: for unsorted input over
+                                      histograms far larger than L2 */
 } sinet_strategy;
 
 /* How membership is looked up. Both are exact. */

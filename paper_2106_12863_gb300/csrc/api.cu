@@ -87,7 +87,7 @@ sinet_status check_params(const sinet_hist_params *p) {
     if (end > (unsigned __int128)UINT64_MAX) return SINET_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (p->policy[c] > 3) return SINET_ERR_INVALID_ARG;
-    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_ATOMIC_NOAGG) return SINET_ERR_INVALID_ARG;
+    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_ATOMIC_CELL) return SINET_ERR_INVALID_ARG;
     if (p->lookup < SINET_LOOKUP_AUTO || p->lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
     if (p->block_threads && (p->block_threads > 1024 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
     return SINET_OK;
@@ -152,6 +152,11 @@ static uint32_t table_smem(const sinet_prefix_table *t, int lk) {
     return 0;
 }
 
+// Histograms at least this large (24 bytes per bin) default to the cell
+// scratch when the input is not time-sorted: well beyond L2, unsorted updates
+// miss, and one sector per update instead of two halves the DRAM traffic.
+static const uint64_t kCellMinHistBytes = 256ull << 20;
+
 // Hot-key cache of the warp-aggregated atomic kernel: 2^9 sets x 4 ways
 // (32 KB of shared memory per CTA).
 static const uint32_t kCacheSetBits = 9;
@@ -198,6 +203,8 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
             strat = SINET_STRAT_SMEM_FULL;
         else if (p->hints & SINET_HINT_TIME_SORTED)
             strat = SINET_STRAT_PRIV_TILE;
+        else if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4)
+            strat = SINET_STRAT_ATOMIC_CELL;
         else
             strat = SINET_STRAT_GLOBAL_ATOMIC;
     }
@@ -232,8 +239,14 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     if (strat == SINET_STRAT_SORT_REDUCE && r.g.n * (h.two_dir ? 2ull : 1ull) >= 0xFFFFFFF0ull)
         return SINET_ERR_UNSUPPORTED;
 
-    st = zero_outputs(p, o, s);
-    if (st != SINET_OK) return st;
+    if (strat == SINET_STRAT_ATOMIC_CELL && !p->accumulate && r.g.n > 0) {
+        // the expansion writes every bin; only the counters start at zero
+        cudaError_t ez = cudaMemsetAsync(o->stats, 0, 64, s);
+        if (ez != cudaSuccess) return cuda_fail(ez);
+    } else {
+        st = zero_outputs(p, o, s);
+        if (st != SINET_OK) return st;
+    }
     if (r.g.n == 0) return SINET_OK;
 
     cudaError_t e = cudaSuccess;
@@ -244,6 +257,18 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         case SINET_STRAT_ATOMIC_NOAGG:
             e = run_fused_atomic(lk, false, r, ta_tab, h, 0, c);
             break;
+        case SINET_STRAT_ATOMIC_CELL: {
+            // zeroed cells, the combining kernel into them, then the expansion
+            const size_t cell_bytes = 32 * (size_t)p->n_bins;
+            e = cudaMallocAsync(reinterpret_cast<void **>(&h.cells), cell_bytes, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            e = cudaMemsetAsync(h.cells, 0, cell_bytes, s);
+            if (e == cudaSuccess) e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c);
+            if (e == cudaSuccess) e = run_cells_expand(h, p->accumulate != 0, c);
+            const cudaError_t e2 = cudaFreeAsync(h.cells, s);
+            if (e == cudaSuccess) e = e2;
+            break;
+        }
         case SINET_STRAT_PRIV_TILE:
         case SINET_STRAT_SMEM_FULL:
             e = run_fused_tile(lk, r, ta_tab, h, ta, ct);

@@ -235,6 +235,29 @@ __global__ void __launch_bounds__(1024) k_fused_tile(RecArgs r, TableArgs t, His
 }
 
 // ---------------------------------------------------------------------------
+// Cell expansion: one thread per bin reads its 32-byte cell and writes (or
+// adds to) the four output arrays; consecutive threads write consecutive bins.
+__global__ void __launch_bounds__(256) k_cells_expand(HistArgs h, uint32_t accumulate) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < h.n_bins; b += stride) {
+        const ulonglong2 sums = __ldcs(reinterpret_cast<const ulonglong2 *>(h.cells + 4 * b));
+        const ulonglong2 cnts = __ldcs(reinterpret_cast<const ulonglong2 *>(h.cells + 4 * b + 2));
+        uint32_t c0 = (uint32_t)cnts.x, c1 = (uint32_t)(cnts.x >> 32);
+        uint64_t s0 = sums.x, s1 = sums.y;
+        if (accumulate) {
+            c0 += h.cnt[0][b];
+            c1 += h.cnt[1][b];
+            s0 += h.byt[0][b];
+            s1 += h.byt[1][b];
+        }
+        h.cnt[0][b] = c0;
+        h.cnt[1][b] = c1;
+        h.byt[0][b] = s0;
+        h.byt[1][b] = s1;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers.
 
 size_t smem_optin_limit() {
@@ -257,6 +280,12 @@ static cudaError_t launch(K kernel, size_t smem, const LaunchCfg &c, int &grid) 
         grid = per_sm * c.sm_count;
     }
     return cudaSuccess;
+}
+
+cudaError_t run_cells_expand(const HistArgs &h, bool accumulate, const LaunchCfg &c) {
+    const int grid = 8 * c.sm_count;
+    k_cells_expand<<<grid, 256, 0, c.stream>>>(h, accumulate ? 1u : 0u);
+    return cudaGetLastError();
 }
 
 cudaError_t run_discriminate(int lk, const RecArgs &r, const TableArgs &t, uint64_t *counts,

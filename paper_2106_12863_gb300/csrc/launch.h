@@ -34,6 +34,10 @@ cudaError_t run_fused_atomic(int lk, bool agg, const RecArgs &r, const TableArgs
 cudaError_t run_fused_tile(int lk, const RecArgs &r, const TableArgs &t, const HistArgs &h,
                            const TileArgs &ta, const LaunchCfg &c);
 
+// Expand per-bin cells (see HistArgs::cells) into the output arrays of h,
+// adding to them when accumulate is set.
+cudaError_t run_cells_expand(const HistArgs &h, bool accumulate, const LaunchCfg &c);
+
 // Largest dynamic shared memory a CTA may use on this device.
 size_t smem_optin_limit();
 

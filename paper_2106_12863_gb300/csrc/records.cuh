@@ -33,6 +33,10 @@ struct HistArgs {
     uint32_t two_dir; // some class routes to both directions
     uint32_t n_bins;
     uint32_t *status;  // device status word
+    // When set, updates go to one 32-byte cell per bin instead of the four
+    // output arrays: u64 byte sums of directions 0 and 1, then their u32
+    // counts (one DRAM sector per update where the arrays would touch two).
+    uint64_t *cells;
 };
 
 // ---------------------------------------------------------------------------
@@ -318,6 +322,12 @@ __device__ __forceinline__ void flush_counters(uint64_t *stats, const uint32_t c
 }
 
 __device__ __forceinline__ void gadd(const HistArgs &h, uint32_t d, uint32_t bin, uint32_t c, uint64_t s) {
+    if (h.cells) {
+        uint64_t *cell = h.cells + 4 * (uint64_t)bin;
+        red_add_u64(cell + d, s);
+        red_add_u32(reinterpret_cast<uint32_t *>(cell + 2) + d, c);
+        return;
+    }
     uint32_t *cp = d ? h.cnt[1] : h.cnt[0];
     uint64_t *bp = d ? h.byt[1] : h.byt[0];
     red_add_u32(cp + bin, c);

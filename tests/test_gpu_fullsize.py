@@ -75,7 +75,7 @@ def _check_sampled(orc, net, ln, rec, w, got, policy, seed, hot):
 
 
 @pytest.mark.parametrize("key,strategy,other,hot", [("day", "priv_tile", "global_atomic", (0, 500)),
-                                                    ("heavy", "global_atomic", "atomic_noagg", (1000, 1020))])
+                                                    ("heavy", "atomic_cell", "global_atomic", (1000, 1020))])
 def test_full_workload(orc, key, strategy, other, hot):
     w = gen.WORKLOADS[key]
     net, ln, h = _pinned(w)

@@ -24,7 +24,7 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU too
 
 import paper_2106_12863_gb300 as sinet  # noqa: E402
 
-STRATS = ["global_atomic", "atomic_noagg", "priv_tile", "sort_reduce"]
+STRATS = ["global_atomic", "atomic_noagg", "atomic_cell", "priv_tile", "sort_reduce"]
 POLICIES = {"exclusive": sinet.EXCLUSIVE, "inclusive": sinet.INCLUSIVE, "paper_alg1": sinet.PAPER_ALG1}
 
 
