@@ -35,6 +35,13 @@ sinet_status device_state(DeviceState **out) {
         d.smem_per_sm = (size_t)v;
         SINET_CUDA(cudaMalloc(&d.status, 256));
         SINET_CUDA(cudaMemset(d.status, 0, 256));
+        // keep stream-ordered scratch cached in the device's default pool
+        // between calls instead of returning it at every synchronisation
+        cudaMemPool_t pool = nullptr;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
         d.ready = true;
     }
     *out = &d;
