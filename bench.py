@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-post", action="store_true", help="skip the roll-up / sparse timings")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -857,6 +858,36 @@ def main():
                          "ms_per_step": e2e_ms, "steps": args.e2e_steps}
         st2 = hout["stats"].numpy().view(np.uint64)
         assert np.array_equal(st2, stats), "e2e result differs from the resident run"
+
+    # post-processing of the day histogram: hourly and ten-minute roll-ups and
+    # the sparse form (each reads the 24 B per bin of the dense histogram)
+    if not args.no_post and w.bin_width == 1:
+        post = {}
+        hist_bytes = BIN_BYTES * w.n_bins
+        for name, fn in (("rollup_10min", lambda: sinet.rollup(out, 600_000, out=coarse10)),
+                         ("rollup_1h", lambda: sinet.rollup(out, 3_600_000, out=coarse1h)),
+                         ("sparse", lambda: sinet.sinet_histogram_sparse(
+                             out.c(), w.n_bins, sp_bin, sp_c[0], sp_c[1], sp_b[0], sp_b[1], w.n_bins, sp_n))):
+            if name == "rollup_10min":
+                coarse10 = sinet.Histogram(-(-w.n_bins // 600_000), dev, zero=False)
+                coarse1h = sinet.Histogram(-(-w.n_bins // 3_600_000), dev, zero=False)
+                sp_bin = torch.empty(w.n_bins, dtype=torch.int32, device=dev)
+                sp_c = torch.empty((2, w.n_bins), dtype=torch.int32, device=dev)
+                sp_b = torch.empty((2, w.n_bins), dtype=torch.int64, device=dev)
+                sp_n = torch.zeros(1, dtype=torch.int64, device=dev)
+            fn()
+            torch.cuda.synchronize()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for _ in range(5):
+                fn()
+            p1.record(stream)
+            torch.cuda.synchronize()
+            ms = p0.elapsed_time(p1) / 5
+            post[name] = {"ms": ms, "input_GBs": hist_bytes / (ms / 1e3) / 1e9}
+        post["sparse"]["bins"] = int(sp_n.item())
+        result["post"] = post
+        del sp_bin, sp_c, sp_b
 
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)

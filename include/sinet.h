@@ -408,6 +408,32 @@ sinet_status sinet_server_stats(sinet_server *s, int reset, sinet_server_counter
 /* Stop the worker (requests not yet done are dropped), free everything. */
 sinet_status sinet_server_destroy(sinet_server *s);
 
+/* ------------------------------------------------------------------------
+ * Post-processing of a histogram on the device (the coarser views of
+ * Section 6: hourly and ten-minute series; the present-keys output of the
+ * reduce-by-key of Section 5).
+ */
+
+/* Roll a histogram of n_bins bins up into ceil(n_bins / factor) coarser bins:
+ * out bin j = the sum of in bins [j * factor, (j + 1) * factor) in both
+ * directions (counts modulo 2^32, byte sums modulo 2^64), which equals the
+ * histogram taken directly with bin width factor * w at the same t0. out's
+ * arrays hold ceil(n_bins / factor) entries and must not overlap in's; with
+ * accumulate = 0 they are overwritten, else added to. in->stats is copied to
+ * out->stats when both are given. Device pointers; asynchronous on stream. */
+sinet_status sinet_histogram_rollup(const sinet_hist_out *in, uint64_t n_bins, uint64_t factor, int accumulate,
+                                    const sinet_hist_out *out, sinet_stream_t stream);
+
+/* Sparse form: the bins with a non-zero count or byte sum in either
+ * direction, in increasing bin order, as parallel device arrays (bin index,
+ * count per direction, byte sum per direction) of capacity cap. The number
+ * of such bins is written to the device word *d_n_out; when it exceeds cap,
+ * only the first cap are written. Asynchronous on stream (one small
+ * stream-ordered scratch allocation). */
+sinet_status sinet_histogram_sparse(const sinet_hist_out *in, uint64_t n_bins, uint32_t *d_bin, uint32_t *d_count0,
+                                    uint32_t *d_count1, uint64_t *d_bytes0, uint64_t *d_bytes1, uint64_t cap,
+                                    uint64_t *d_n_out, sinet_stream_t stream);
+
 /*
  * Read and clear the device status word of the current device, after
  * synchronising `stream`. *device_code receives the latched sinet_status

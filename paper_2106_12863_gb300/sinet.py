@@ -123,6 +123,9 @@ def load():
         "sinet_batch_strategy": (ctypes.c_int, [_P, u32, _P]),
         "sinet_batch_info": (ctypes.c_int, [_P, _P, _P]),
         "sinet_batch_destroy": (ctypes.c_int, [_P]),
+        "sinet_histogram_rollup": (ctypes.c_int, [ctypes.POINTER(HistOutC), u64, u64, ctypes.c_int,
+                                                  ctypes.POINTER(HistOutC), _P]),
+        "sinet_histogram_sparse": (ctypes.c_int, [ctypes.POINTER(HistOutC), u64, _P, _P, _P, _P, _P, u64, _P, _P]),
         "sinet_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfigC), ctypes.POINTER(TenantC), u32, _P]),
         "sinet_server_submit": (ctypes.c_int, [_P, u32, _P, _P, _P, _P, u64, _P]),
         "sinet_server_wait": (ctypes.c_int, [_P, u64, u32, _P]),
@@ -277,6 +280,19 @@ def sinet_device_status(stream=None) -> int:
     v = ctypes.c_uint32()
     _check(load().sinet_device_status(_stream(stream), ctypes.byref(v)), "sinet_device_status")
     return int(v.value)
+
+
+def sinet_histogram_rollup(inp: HistOutC, n_bins: int, factor: int, accumulate: bool, out: HistOutC,
+                           stream=None):
+    _check(load().sinet_histogram_rollup(ctypes.byref(inp), n_bins, factor, int(accumulate),
+                                         ctypes.byref(out), _stream(stream)), "sinet_histogram_rollup")
+
+
+def sinet_histogram_sparse(inp: HistOutC, n_bins: int, d_bin, d_count0, d_count1, d_bytes0, d_bytes1,
+                           cap: int, d_n_out, stream=None):
+    _check(load().sinet_histogram_sparse(ctypes.byref(inp), n_bins, _dptr(d_bin), _dptr(d_count0),
+                                         _dptr(d_count1), _dptr(d_bytes0), _dptr(d_bytes1), cap,
+                                         _dptr(d_n_out), _stream(stream)), "sinet_histogram_sparse")
 
 
 def sinet_batch_create(slices, flags: int = 0, stream=None) -> int:
@@ -529,3 +545,29 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def rollup(hist: "Histogram", factor: int, out: "Histogram | None" = None, accumulate: bool = False,
+           stream=None) -> "Histogram":
+    """Coarser bins: out bin j sums bins [j * factor, (j + 1) * factor)."""
+    n_out = -(-hist.n_bins // factor)
+    out = out or Histogram(n_out, hist.count.device, zero=False)
+    sinet_histogram_rollup(hist.c(), hist.n_bins, factor, accumulate, out.c(), stream)
+    return out
+
+
+def sparse(hist: "Histogram", cap: int | None = None, stream=None) -> dict:
+    """Non-empty bins in order: {"n": total, "bin", "count" [2, k], "bytes" [2, k]} (device
+    tensors; k = min(total, cap))."""
+    import torch
+
+    dev = hist.count.device
+    cap = hist.n_bins if cap is None else cap
+    b = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    c = torch.empty((2, max(cap, 1)), dtype=torch.int32, device=dev)
+    y = torch.empty((2, max(cap, 1)), dtype=torch.int64, device=dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    sinet_histogram_sparse(hist.c(), hist.n_bins, b, c[0], c[1], y[0], y[1], cap, n, stream)
+    total = int(n.item())
+    k = min(total, cap)
+    return {"n": total, "bin": b[:k], "count": c[:, :k], "bytes": y[:, :k]}
