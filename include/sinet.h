@@ -276,6 +276,14 @@ typedef struct {
                                          lookup: AUTO or INTERVAL; hints, tile_bins and
                                          block_threads are ignored */
     sinet_hist_out out;               /* device outputs; must outlive the batch */
+    const uint32_t *ready;            /* optional device word: when non-NULL the slice's work
+                                         items wait until it equals ready_value, so its records
+                                         can still be landing (a copy on another stream that ends
+                                         by writing the word) when the launch starts. A wait is
+                                         bounded (sinet_batch_set_wait); an item whose wait runs
+                                         out is left out and SINET_ERR_TIMEOUT is latched in the
+                                         device status word. */
+    uint32_t ready_value;
 } sinet_batch_slice;
 
 /* Flags of sinet_batch_create. */
@@ -310,6 +318,10 @@ sinet_status sinet_batch_create(const sinet_batch_slice *slices, uint32_t n_slic
 /* Enqueue one run of the batch on `stream` (a graph launch). Non-accumulating
  * slices' outputs are zeroed first; accumulating slices are added to. */
 sinet_status sinet_batch_run(sinet_batch *b, sinet_stream_t stream);
+
+/* Bound, in nanoseconds of the GPU's global timer, of a work item's wait on
+ * its slice's ready word (default 2 s). Synchronous. */
+sinet_status sinet_batch_set_wait(sinet_batch *b, uint64_t wait_ns);
 
 /* The strategy (sinet_strategy) the batch runs for slice i, after tuning. */
 sinet_status sinet_batch_strategy(const sinet_batch *b, uint32_t i, int32_t *strategy);

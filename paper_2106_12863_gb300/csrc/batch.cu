@@ -347,6 +347,25 @@ __device__ __forceinline__ void item_tile(const Classifier<LK> &C, uint64_t q0, 
     }
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Poll a ready word until it holds `want` or `limit_ns` pass; the acquire
+// fence orders the record loads after the observed value.
+__device__ bool wait_ready(const uint32_t *word, uint32_t want, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(word) : "memory");
+        if (v == want) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+        __nanosleep(200);
+    }
+}
+
 // Called (not inlined) once per work item, so each lookup form gets its own
 // register allocation. Shared-memory addresses are rebuilt here from the
 // dynamic shared array and a byte offset: a pointer passed in would be a
@@ -375,7 +394,7 @@ __device__ __noinline__ void run_item(uint32_t work_off, uint64_t q0, uint64_t q
 __global__ void __launch_bounds__(kBatchBlock, 2) k_batch(BatchArgs b, uint32_t *status) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t bar;
-    __shared__ uint32_t s_item, s_slice, s_lo, s_hi;
+    __shared__ uint32_t s_item, s_slice, s_lo, s_hi, s_ok;
     __shared__ unsigned long long s_cnt[6];
     // first work item of every slice, when the batch is small enough to keep it here
     __shared__ uint32_t s_starts[kBatchSmemStarts + 1];
@@ -417,6 +436,16 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch(BatchArgs b, uint32_t 
             reinterpret_cast<uint32_t *>(&g_desc)[i] = reinterpret_cast<const uint32_t *>(b.slices + si)[i];
         __syncthreads();
         const BatchSlice &S = g_desc;
+        if (S.ready) {
+            // the slice's records are still being filled (by a copy on another
+            // stream): wait, bounded, for its ready word
+            if (threadIdx.x == 0) s_ok = wait_ready(S.ready, S.ready_value, b.hdr->wait_ns) ? 1u : 0u;
+            __syncthreads();
+            if (!s_ok) {
+                if (threadIdx.x == 0) latch_status(status, SINET_ERR_TIMEOUT);
+                continue;  // the item is left out; the status word says so
+            }
+        }
         const uint32_t lk = S.lk;
         uint32_t tbytes = 0;
         if (lk != LK_INTERVAL_GLOBAL) {

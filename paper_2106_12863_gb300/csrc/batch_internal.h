@@ -59,6 +59,7 @@ struct BatchEngine {
     size_t bytes = 0;
     size_t off_item = 0, off_zero = 0, off_slices = 0;
     BatchArgs args{};
+    uint64_t wait_ns = 2000000000ull;  // bound of a ready-word wait
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 

@@ -1,6 +1,7 @@
 // Batched launch runtime: slice planning, the strategy autotuner and its
 // cache, the device engine (descriptors + CUDA graph), and the batch C ABI.
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -87,6 +88,8 @@ sinet_status plan_slice(const sinet_batch_slice &u, const DeviceState *ds, uint3
     d.tile_bins = (uint32_t)std::min<uint64_t>(T, 0xFFFFFFFFull);
     ps.tile_fits = staged + 16 * T <= smem;
     d.zero = u.params.accumulate ? 0u : 1u;
+    d.ready = u.ready;
+    d.ready_value = u.ready_value;
     if (u.params.strategy == SINET_STRAT_SMEM_FULL && !ps.tile_fits) return SINET_ERR_UNSUPPORTED;
     set_strategy(ps, u.params.strategy, batch_grid(ds));  // AUTO: resolved later
     ps.zero_items = d.zero ? (uint32_t)((u.params.n_bins + kZeroBins - 1) / kZeroBins) : 0u;
@@ -136,6 +139,7 @@ void BatchEngine::image(const std::vector<PlannedSlice> &v, std::vector<uint8_t>
     item[n] = (uint32_t)ti;
     zero[n] = (uint32_t)tz;
     hdr.n_slices = n;
+    hdr.wait_ns = wait_ns;
     hdr.total_items = (uint32_t)ti;
     hdr.total_zero = (uint32_t)tz;
     std::memcpy(buf.data(), &hdr, sizeof hdr);
@@ -451,6 +455,14 @@ sinet_status sinet_batch_run(sinet_batch *b, sinet_stream_t stream) {
     SINET_CUDA(cudaGetDevice(&dev));
     if (dev != b->eng.device) return SINET_ERR_INVALID_ARG;
     return b->eng.launch(stream);
+}
+
+sinet_status sinet_batch_set_wait(sinet_batch *b, uint64_t wait_ns) {
+    if (!b) return SINET_ERR_INVALID_ARG;
+    b->eng.wait_ns = wait_ns;
+    SINET_CUDA(cudaMemcpy(reinterpret_cast<uint8_t *>(b->eng.d_mem) + offsetof(BatchHeader, wait_ns), &wait_ns,
+                          sizeof wait_ns, cudaMemcpyHostToDevice));
+    return SINET_OK;
 }
 
 sinet_status sinet_batch_strategy(const sinet_batch *b, uint32_t i, int32_t *strategy) {

@@ -62,7 +62,8 @@ struct BatchSlice {
     uint32_t tile_bins;  // BS_TILE: bins per direction of the tile (>= n_bins, multiple of 4)
     uint32_t zero;       // 1: the outputs are zeroed by the launch (not accumulated into)
     uint32_t item_quads; // quads per work item of this slice
-    uint32_t pad;
+    uint32_t ready_value;       // with `ready`: the value that means the records are in place
+    const uint32_t *ready;      // optional device word; items wait (bounded) until it equals ready_value
 };
 
 // Device-resident header read by both batch kernels at every launch, so one
@@ -73,7 +74,8 @@ struct BatchHeader {
     uint32_t total_items;  // work items of all slices
     uint32_t total_zero;   // zeroing items of all slices
     uint32_t counter;      // work-item counter, reset by the zeroing kernel
-    uint32_t pad[3];
+    uint32_t pad;
+    uint64_t wait_ns;      // bound of a wait on a slice's ready word (global timer, ns)
 };
 
 // Device arrays of a batch (all device pointers).

@@ -14,10 +14,31 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cuda.h>
+
 #include "batch_internal.h"
 
 namespace sinet {
 namespace {
+
+// The driver's stream write (a front-end operation: it needs no SM) ends a
+// request's copies by setting its ready word, so a launch can start while
+// the copies are still landing.
+typedef CUresult (*StreamWriteValue32)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+
+StreamWriteValue32 stream_write_fn() {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return reinterpret_cast<StreamWriteValue32>(fn);
+}
+
+// Value of a request's ready word: never 0 (the words start at 0), and
+// distinct for tickets less than 2^32 - 1 apart.
+uint32_t ready_value(uint64_t ticket) { return 1u + (uint32_t)(ticket % 0xFFFFFFFFull); }
 
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -81,6 +102,7 @@ struct Request {
     const uint32_t *src = nullptr, *dst = nullptr, *by = nullptr;
     uint64_t n = 0;
     size_t off = 0, bytes = 0;
+    uint32_t slot = 0;  // index of its ready word
     uint64_t submit_ns = 0, done_ns = 0, launch = 0;
     bool done = false;
 };
@@ -107,6 +129,9 @@ struct sinet_server {
     uint8_t *stage = nullptr;  // pinned host image of the launch's descriptors
     cudaStream_t copy_stream = nullptr, compute_stream = nullptr;
     cudaEvent_t copied = nullptr, launch_done = nullptr;
+    uint32_t *flags = nullptr;          // ready words, one per admission slot
+    std::vector<uint32_t> free_slots;   // admission slots not in use
+    sinet::StreamWriteValue32 write32 = nullptr;  // null: launches wait on the copy event instead
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -147,6 +172,10 @@ sinet_status plan_launch(sinet_server *s, const std::vector<Request *> &reqs, st
         u.params = t.params;
         u.params.strategy = t.strategy;
         u.out = t.out;
+        if (s->write32 && r->n) {
+            u.ready = s->flags + r->slot;
+            u.ready_value = ready_value(r->ticket);
+        }
         const sinet_status st = plan_slice(u, s->ds, s->smem, v[i]);
         if (st != SINET_OK) return st;
     }
@@ -160,6 +189,7 @@ void finish_launch(sinet_server *s) {
         r->done = true;
         r->done_ns = t;
         s->arena.release(r->off, r->bytes);
+        s->free_slots.push_back(r->slot);
         s->latencies.push_back(t - r->submit_ns);
         s->requests_done++;
         s->records_done += r->n;
@@ -182,8 +212,11 @@ void worker_main(sinet_server *s) {
         while (!s->pending.empty() && s->error == SINET_OK) {
             Request *r = s->pending.front();
             size_t off = 0;
-            if (r->n && !s->arena.alloc(r->bytes, &off)) break;
+            if (s->free_slots.empty()) break;  // admission by slot ...
+            if (r->n && !s->arena.alloc(r->bytes, &off)) break;  // ... and by HBM budget
             r->off = off;
+            r->slot = s->free_slots.back();
+            s->free_slots.pop_back();
             s->pending.pop_front();
             if (r->n) {
                 uint8_t *base = s->arena_mem + off;
@@ -197,6 +230,11 @@ void worker_main(sinet_server *s) {
                     e = cudaMemcpyAsync(base + o2, r->dst, 4 * r->n, cudaMemcpyHostToDevice, s->copy_stream);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(base + o3, r->by, 4 * r->n, cudaMemcpyHostToDevice, s->copy_stream);
+                if (e == cudaSuccess && s->write32 &&
+                    s->write32(reinterpret_cast<CUstream>(s->copy_stream),
+                               reinterpret_cast<CUdeviceptr>(s->flags + r->slot), ready_value(r->ticket),
+                               CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
+                    e = cudaErrorUnknown;
                 lk.lock();
                 if (e != cudaSuccess) s->error = cuda_fail(e);
             }
@@ -221,9 +259,13 @@ void worker_main(sinet_server *s) {
             if (st == SINET_OK) {
                 s->eng.image(plan, img);
                 std::memcpy(s->stage, img.data(), img.size());
-                // the launch waits for every copy issued so far
-                e = cudaEventRecord(s->copied, s->copy_stream);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->compute_stream, s->copied, 0);
+                // the launch starts at once and each request's work waits for
+                // its ready word; without stream writes it waits for every
+                // copy issued so far
+                if (!s->write32) {
+                    e = cudaEventRecord(s->copied, s->copy_stream);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->compute_stream, s->copied, 0);
+                }
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(s->eng.d_mem, s->stage, img.size(), cudaMemcpyHostToDevice,
                                         s->compute_stream);
@@ -311,15 +353,31 @@ sinet_status sinet_server_create(const sinet_server_config *cfg, const sinet_ten
                          : 24 * nb <= (64ull << 20) ? SINET_STRAT_GLOBAL_ATOMIC
                                                     : SINET_STRAT_ATOMIC_NOAGG;
     }
+    // admission slots (each with a ready word): four launches' worth
+    const uint32_t slots = 4 * cfg->max_requests_per_launch;
+    if (e == cudaSuccess && st == SINET_OK) e = cudaMalloc(&s->flags, 4 * (size_t)slots);
+    if (e == cudaSuccess && st == SINET_OK) e = cudaMemset(s->flags, 0, 4 * (size_t)slots);
+    for (uint32_t i = 0; i < slots; ++i) s->free_slots.push_back(slots - 1 - i);
     if (e == cudaSuccess && st == SINET_OK) e = cudaMalloc(&s->arena_mem, cfg->inflight_budget_bytes);
     if (e == cudaSuccess) s->arena.init(cfg->inflight_budget_bytes);
     if (e == cudaSuccess && st == SINET_OK) st = s->eng.init(cfg->max_requests_per_launch, ds, s->smem);
+    // a request's items may wait behind every copy admitted before it
+    s->eng.wait_ns = 30000000000ull;
     if (e == cudaSuccess && st == SINET_OK) e = cudaMallocHost(&s->stage, s->eng.bytes);
     if (e == cudaSuccess && st == SINET_OK) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && st == SINET_OK) e = cudaStreamCreateWithFlags(&s->compute_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && st == SINET_OK) e = cudaEventCreateWithFlags(&s->copied, cudaEventDisableTiming);
     if (e == cudaSuccess && st == SINET_OK) e = cudaEventCreateWithFlags(&s->launch_done, cudaEventDisableTiming);
     if (e == cudaSuccess && st == SINET_OK) st = s->eng.capture(ds->status);
+    if (e == cudaSuccess && st == SINET_OK) {
+        // stream writes in use only if one goes through here
+        s->write32 = stream_write_fn();
+        if (s->write32 &&
+            (s->write32(reinterpret_cast<CUstream>(s->copy_stream), reinterpret_cast<CUdeviceptr>(s->flags), 0,
+                        CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS ||
+             cudaStreamSynchronize(s->copy_stream) != cudaSuccess))
+            s->write32 = nullptr;
+    }
     if (e != cudaSuccess && st == SINET_OK) st = cuda_fail(e);
     if (st == SINET_OK) {
         s->worker = std::thread(worker_main, s);
@@ -447,6 +505,7 @@ sinet_status sinet_server_destroy(sinet_server *s) {
     for (Tenant &t : s->tenants)
         if (t.out.count[0]) cudaFree(t.out.count[0]);
     if (s->arena_mem) cudaFree(s->arena_mem);
+    if (s->flags) cudaFree(s->flags);
     s->eng.release();
     if (s->stage) cudaFreeHost(s->stage);
     if (s->copied) cudaEventDestroy(s->copied);

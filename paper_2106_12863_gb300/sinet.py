@@ -61,7 +61,8 @@ class HistOutC(ctypes.Structure):
 class BatchSliceC(ctypes.Structure):
     _fields_ = [("ts", ctypes.c_void_p), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
                 ("bytes", ctypes.c_void_p), ("n", ctypes.c_uint64), ("table", ctypes.c_void_p),
-                ("params", HistParamsC), ("out", HistOutC)]
+                ("params", HistParamsC), ("out", HistOutC), ("ready", ctypes.c_void_p),
+                ("ready_value", ctypes.c_uint32)]
 
 
 BATCH_AUTOTUNE = 1
@@ -121,6 +122,7 @@ def load():
         "sinet_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchSliceC), u32, u32, _P, _P]),
         "sinet_batch_run": (ctypes.c_int, [_P, _P]),
         "sinet_batch_strategy": (ctypes.c_int, [_P, u32, _P]),
+        "sinet_batch_set_wait": (ctypes.c_int, [_P, u64]),
         "sinet_batch_info": (ctypes.c_int, [_P, _P, _P]),
         "sinet_batch_destroy": (ctypes.c_int, [_P]),
         "sinet_histogram_rollup": (ctypes.c_int, [ctypes.POINTER(HistOutC), u64, u64, ctypes.c_int,
@@ -432,11 +434,15 @@ class Batch:
     HistParams, out: Histogram). The tensors, tables and outputs are referenced
     by the batch and kept alive here."""
 
-    def __init__(self, slices, autotune: bool = False, stream=None):
+    def __init__(self, slices, autotune: bool = False, stream=None, ready=None):
+        """``ready``: optional per-slice (device uint32 tensor view of one word, value) or None."""
         self._keep = list(slices)
+        self._ready = list(ready) if ready is not None else [None] * len(self._keep)
         cs = []
-        for table, ts, src, dst, nb, params, out in self._keep:
+        for (table, ts, src, dst, nb, params, out), rd in zip(self._keep, self._ready):
             c = BatchSliceC()
+            if rd is not None:
+                c.ready, c.ready_value = _dptr(rd[0]), rd[1]
             c.ts, c.src, c.dst, c.bytes = _dptr(ts), _dptr(src), _dptr(dst), _dptr(nb)
             c.n = ts.numel()
             c.table = table.handle
@@ -447,6 +453,9 @@ class Batch:
 
     def run(self, stream=None):
         sinet_batch_run(self.handle, stream)
+
+    def set_wait(self, wait_ns: int):
+        _check(load().sinet_batch_set_wait(self.handle, wait_ns), "sinet_batch_set_wait")
 
     def strategy(self, i: int) -> str:
         v = sinet_batch_strategy(self.handle, i)

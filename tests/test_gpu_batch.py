@@ -175,3 +175,50 @@ def test_batch_autotune_and_cache(orc, tmp_path, monkeypatch):
         assert b2.strategy(i) == b.strategy(i)
     b.close()
     b2.close()
+
+
+def test_batch_ready_word_timeout(orc):
+    """A slice whose ready word is never set: its items wait out the bound,
+    are left out, and the device status says SINET_ERR_TIMEOUT; the other
+    slices are exact."""
+    cases = _generated(3, 0.005, ["global_atomic", "atomic_noagg", "smem_full"])
+    word = torch.zeros(4, dtype=torch.int32, device="cuda")
+    b = sinet.Batch([c.slice() for c in cases], ready=[None, (word[0:1], 1), None])
+    b.set_wait(2_000_000)  # 2 ms
+    b.run()
+    torch.cuda.synchronize()
+    assert sinet.sinet_device_status() == 5  # SINET_ERR_TIMEOUT, now cleared
+    for i in (0, 2):
+        assert_hist_equal(cases[i].out.to_numpy(), cases[i].want(orc), f"slice {i}")
+    left = cases[1].out.to_numpy()
+    assert not left["count"].any() and not left["bytes"].any()  # zeroed, never filled
+    b.close()
+
+
+def test_batch_ready_word_set_by_a_copy_on_another_stream(orc):
+    """The launch starts before a copy on another stream has filled a slice's
+    records; the slice's items wait for the ready word the copy stream writes
+    after the records and then see the copied records."""
+    cases = _generated(4, 0.01, ["global_atomic", "atomic_noagg", "auto", "auto"])
+    target = cases[2]
+    real = {k: v.clone() for k, v in target.dev.items()}
+    for v in target.dev.values():
+        v.zero_()  # the launch must not see these
+    host = {k: v.cpu().pin_memory() for k, v in real.items()}
+    word = torch.zeros(1, dtype=torch.int32, device="cuda")
+    seven = torch.full((1,), 7, dtype=torch.int32).pin_memory()
+    b = sinet.Batch([c.slice() for c in cases], ready=[None, None, (word, 7), None])
+    side = torch.cuda.Stream()
+    filler = torch.empty(1 << 28, dtype=torch.uint8).pin_memory()  # 256 MB ahead of the records
+    filler_dev = torch.empty_like(filler, device="cuda")
+    b.run()  # on the current stream
+    with torch.cuda.stream(side):
+        filler_dev.copy_(filler, non_blocking=True)
+        for k, v in target.dev.items():
+            v.copy_(host[k], non_blocking=True)
+        word.copy_(seven, non_blocking=True)
+    torch.cuda.synchronize()
+    assert sinet.sinet_device_status() == 0
+    for i, c in enumerate(cases):
+        assert_hist_equal(c.out.to_numpy(), c.want(orc), f"slice {i}")
+    b.close()
