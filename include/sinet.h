@@ -86,6 +86,8 @@ typedef enum {
 /* Input hints (sinet_hist_params.hints). */
 #define SINET_HINT_TIME_SORTED 1u  /* records are (nearly) sorted by ts */
 
+typedef struct sinet_prefix_table sinet_prefix_table;
+
 typedef struct {
     uint64_t t0_ms;        /* window start */
     uint64_t bin_width_ms; /* >= 1 */
@@ -97,6 +99,11 @@ typedef struct {
     uint32_t hints;        /* SINET_HINT_* */
     uint32_t tile_bins;    /* PRIV_TILE bins per direction per tile (0 = default) */
     uint32_t block_threads;/* threads per CTA (0 = default) */
+    const struct sinet_prefix_table *watch; /* optional watch list (the blocklist views of Section 6):
+                              only records whose src or dst is in it are classified and binned,
+                              every other record counts in stats[6]. Runs with GLOBAL_ATOMIC,
+                              ATOMIC_NOAGG and ATOMIC_CELL (AUTO picks among them);
+                              sinet_discriminate_histogram only. NULL = no filter. */
 } sinet_hist_params;
 
 /*
@@ -104,7 +111,8 @@ typedef struct {
  *   count[d]: uint32[n_bins]  (sessions per bin; wraps modulo 2^32 when accumulating)
  *   bytes[d]: uint64[n_bins]  (sum of the records' bytes field)
  *   stats:    uint64[8]       (records per class [0..3], out-of-window records per
- *                              routed direction [4..5], reserved [6..7])
+ *                              routed direction [4..5], records left out by the watch
+ *                              list [6], reserved [7])
  * A record routed to direction d whose ts lies outside the window is not
  * binned; it is counted in stats[4 + d].
  */
@@ -114,8 +122,7 @@ typedef struct {
     uint64_t *stats;
 } sinet_hist_out;
 
-/* Opaque, library-owned, device-resident compiled CIDR list. */
-typedef struct sinet_prefix_table sinet_prefix_table;
+/* sinet_prefix_table (declared above): opaque, library-owned, device-resident compiled CIDR list. */
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 uint32_t sinet_version(void);
@@ -413,6 +420,13 @@ sinet_status sinet_server_tenant_output(sinet_server *s, uint32_t tenant, sinet_
  * result that includes every submitted request. */
 sinet_status sinet_server_export(sinet_server *s, uint32_t tenant, uint32_t *h_count, uint64_t *h_bytes,
                                  uint64_t *h_stats);
+
+/* The reverse of sinet_server_export: replace a tenant's resident histogram
+ * with host arrays in the same layout (a checkpoint taken earlier, on this
+ * or another server). Waits for the launch in flight, if any; requests
+ * admitted later accumulate onto the imported state. */
+sinet_status sinet_server_import(sinet_server *s, uint32_t tenant, const uint32_t *h_count, const uint64_t *h_bytes,
+                                 const uint64_t *h_stats);
 
 /* Counters and latency percentiles; reset = 1 clears them afterwards. */
 sinet_status sinet_server_stats(sinet_server *s, int reset, sinet_server_counters *st);

@@ -42,6 +42,9 @@ def _bind(L):
     L.oracle_discriminate_histogram.argtypes = [P, P, ctypes.c_uint32, P, P, P, P, u64, u64, u64,
                                                 u64, P, P, P, P, P, P]
     L.oracle_discriminate_histogram.restype = ctypes.c_int
+    L.oracle_discriminate_histogram_watch.argtypes = [P, P, ctypes.c_uint32, P, P, ctypes.c_uint32, P, P, P,
+                                                      P, u64, u64, u64, u64, P, P, P, P, P, P]
+    L.oracle_discriminate_histogram_watch.restype = ctypes.c_int
     L.oracle_histogram_bins.argtypes = [P, P, ctypes.c_uint32, P, P, P, P, u64, u64, u64, u64, P,
                                         P, u64, P, P]
     L.oracle_histogram_bins.restype = None
@@ -111,6 +114,30 @@ class Oracle:
         c, b, s = h["count"], h["bytes"], h["stats"]
         rc = self.L.oracle_discriminate_histogram(
             net.ctypes.data, ln.ctypes.data, len(net), ts.ctypes.data, src.ctypes.data,
+            dst.ctypes.data, nb.ctypes.data, len(ts), t0, w, n_bins, pol.ctypes.data,
+            c[0].ctypes.data, c[1].ctypes.data, b[0].ctypes.data, b[1].ctypes.data, s.ctypes.data)
+        if rc != 0:
+            raise MemoryError("oracle allocation failed")
+        return h
+
+    def discriminate_histogram_watch(self, net, ln, wnet, wln, rec, t0, w, n_bins, policy=EXCLUSIVE,
+                                     into=None):
+        """Only records with src or dst in the watch list (wnet, wln) are classified and binned;
+        the others count in stats[6]."""
+        h = self.empty_hist(n_bins) if into is None else into
+        net = np.ascontiguousarray(net, np.uint32)
+        ln = np.ascontiguousarray(ln, np.uint8)
+        wnet = np.ascontiguousarray(wnet, np.uint32)
+        wln = np.ascontiguousarray(wln, np.uint8)
+        ts = np.ascontiguousarray(rec["ts"], np.uint64)
+        src = np.ascontiguousarray(rec["src"], np.uint32)
+        dst = np.ascontiguousarray(rec["dst"], np.uint32)
+        nb = np.ascontiguousarray(rec["bytes"], np.uint32)
+        pol = np.asarray(policy, np.uint8)
+        c, b, s = h["count"], h["bytes"], h["stats"]
+        rc = self.L.oracle_discriminate_histogram_watch(
+            net.ctypes.data, ln.ctypes.data, len(net), wnet.ctypes.data if len(wnet) else None,
+            wln.ctypes.data if len(wln) else None, len(wnet), ts.ctypes.data, src.ctypes.data,
             dst.ctypes.data, nb.ctypes.data, len(ts), t0, w, n_bins, pol.ctypes.data,
             c[0].ctypes.data, c[1].ctypes.data, b[0].ctypes.data, b[1].ctypes.data, s.ctypes.data)
         if rc != 0:

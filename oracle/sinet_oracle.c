@@ -23,6 +23,9 @@
  *     count[d][(ts - t0) / w] += 1 (uint32, wraps) and
  *     bytes[d][(ts - t0) / w] += bytes (uint64); otherwise oor[d] += 1.
  *   - stats[0..3] = records per class, stats[4..5] = out-of-range per direction.
+ *   - Watch list (the blocklist analyses of Section 6, as a filter): with a
+ *     second CIDR list, a record whose src and dst are both outside it is not
+ *     classified or binned at all; it only counts in stats[6].
  *
  * Every loop is the definition written out: a loop over records, and for each
  * record a loop over EVERY table entry. No index, no sorting, no early exit.
@@ -184,6 +187,44 @@ int oracle_discriminate_histogram(const uint32_t *net, const uint8_t *len, uint3
                          bytes1, stats);
     }
     free(cls);
+    return 0;
+}
+
+/*
+ * Classification plus histogram of the records whose src or dst is in the
+ * watch list (membership as above, against the second list); every other
+ * record only adds one to stats[6]. Accumulates like oracle_histogram.
+ */
+int oracle_discriminate_histogram_watch(const uint32_t *net, const uint8_t *len, uint32_t n_entries,
+                                        const uint32_t *wnet, const uint8_t *wlen, uint32_t w_entries,
+                                        const uint64_t *ts, const uint32_t *src, const uint32_t *dst,
+                                        const uint32_t *bytes, uint64_t n, uint64_t t0, uint64_t w,
+                                        uint64_t n_bins, const uint8_t *policy, uint32_t *count0,
+                                        uint32_t *count1, uint64_t *bytes0, uint64_t *bytes1,
+                                        uint64_t *stats) {
+    const uint64_t chunk = 1u << 22;
+    uint8_t *cls = (uint8_t *)malloc(chunk);
+    uint8_t *wcls = (uint8_t *)malloc(chunk);
+    if (!cls || !wcls) {
+        free(cls);
+        free(wcls);
+        return -1;
+    }
+    for (uint64_t s = 0; s < n; s += chunk) {
+        uint64_t m = n - s < chunk ? n - s : chunk;
+        oracle_classify(wnet, wlen, w_entries, src + s, dst + s, m, wcls);
+        oracle_classify(net, len, n_entries, src + s, dst + s, m, cls);
+        for (uint64_t i = 0; i < m; i++) {
+            if (wcls[i] == 0) {
+                stats[6] += 1;
+                continue;
+            }
+            oracle_histogram(ts + s + i, bytes + s + i, cls + i, 1, t0, w, n_bins, policy, count0, count1,
+                             bytes0, bytes1, stats);
+        }
+    }
+    free(cls);
+    free(wcls);
     return 0;
 }
 

@@ -205,6 +205,13 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     const uint32_t cap = tile_capacity(ds, tsm);
 
     int strat = p->strategy;
+    const TableArgs *watch = p->watch ? &p->watch->args : nullptr;
+    if (watch && (lk == LK_PML || lk == LK_CLASS_IN)) return SINET_ERR_UNSUPPORTED;
+    if (watch && strat != SINET_STRAT_AUTO && strat != SINET_STRAT_GLOBAL_ATOMIC &&
+        strat != SINET_STRAT_ATOMIC_NOAGG && strat != SINET_STRAT_ATOMIC_CELL)
+        return SINET_ERR_UNSUPPORTED;
+    // a watch list keeps few records (a blocklist): the plain combining kernel
+    if (strat == SINET_STRAT_AUTO && watch) strat = SINET_STRAT_GLOBAL_ATOMIC;
     if (strat == SINET_STRAT_AUTO) {
         if (2ull * p->n_bins <= 8192 && p->n_bins <= cap)
             strat = SINET_STRAT_SMEM_FULL;
@@ -259,10 +266,10 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     cudaError_t e = cudaSuccess;
     switch (strat) {
         case SINET_STRAT_GLOBAL_ATOMIC:
-            e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c);
+            e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c, watch);
             break;
         case SINET_STRAT_ATOMIC_NOAGG:
-            e = run_fused_atomic(lk, false, r, ta_tab, h, 0, c);
+            e = run_fused_atomic(lk, false, r, ta_tab, h, 0, c, watch);
             break;
         case SINET_STRAT_ATOMIC_CELL: {
             // zeroed cells, the combining kernel into them, then the expansion
@@ -270,7 +277,7 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
             e = cudaMallocAsync(reinterpret_cast<void **>(&h.cells), cell_bytes, s);
             if (e != cudaSuccess) return cuda_fail(e);
             e = cudaMemsetAsync(h.cells, 0, cell_bytes, s);
-            if (e == cudaSuccess) e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c);
+            if (e == cudaSuccess) e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c, watch);
             if (e == cudaSuccess) e = run_cells_expand(h, p->accumulate != 0, c);
             const cudaError_t e2 = cudaFreeAsync(h.cells, s);
             if (e == cudaSuccess) e = e2;
@@ -464,6 +471,7 @@ sinet_status sinet_histogram(const uint64_t *d_ts, const uint32_t *d_bytes, cons
     if (n > kMaxN) return SINET_ERR_INVALID_ARG;
     if (n && (!d_ts || !d_bytes || !d_class || !aligned(d_ts, 8) || !aligned(d_bytes, 4)))
         return SINET_ERR_INVALID_ARG;
+    if (p->watch) return SINET_ERR_UNSUPPORTED;  // the class input has no addresses to test
     RecArgs r{};
     r.ts = d_ts;
     r.bytes = d_bytes;

@@ -60,7 +60,7 @@ sinet_status check_slice(const sinet_batch_slice &u) {
     if (s != SINET_STRAT_AUTO && s != SINET_STRAT_GLOBAL_ATOMIC && s != SINET_STRAT_ATOMIC_NOAGG &&
         s != SINET_STRAT_SMEM_FULL)
         return SINET_ERR_UNSUPPORTED;
-    if (u.params.lookup == SINET_LOOKUP_PML) return SINET_ERR_UNSUPPORTED;
+    if (u.params.lookup == SINET_LOOKUP_PML || u.params.watch) return SINET_ERR_UNSUPPORTED;
     return SINET_OK;
 }
 

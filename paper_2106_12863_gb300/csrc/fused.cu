@@ -43,27 +43,58 @@ __global__ void __launch_bounds__(256) k_discriminate(RecArgs r, TableArgs t, ui
     flush_counters(counts, cc, oor, false);
 }
 
-template <int LK, bool AGG>
+// Watch list (the blocklist views of Section 6, as a filter): a record whose
+// src and dst are both outside the second list leaves the quad and counts in
+// `flt` (stats[6]); the list is looked up in its global-memory interval form.
+template <bool WATCH>
+__device__ __forceinline__ void watch_filter(const Classifier<LK_INTERVAL_GLOBAL> &W, Quad &Q, uint32_t &flt) {
+    if (!WATCH) return;
+    uint32_t a[4], ws[4], wd[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = Q.src[j];
+    W.template in_n<4>(a, ws);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = Q.dst[j];
+    W.template in_n<4>(a, wd);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if ((Q.valid >> j & 1u) && !(ws[j] | wd[j])) {
+            Q.valid &= ~(1u << j);
+            flt++;
+        }
+    }
+}
+
+__device__ __forceinline__ void flush_filtered(uint64_t *stats, uint32_t flt) {
+    const uint32_t v = __reduce_add_sync(kFull, flt);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 6), (unsigned long long)v);
+}
+
+template <int LK, bool AGG, bool WATCH>
 __global__ void __launch_bounds__(256, 3) k_fused_atomic(RecArgs r, TableArgs t, HistArgs h,
-                                                         uint32_t cache_set_bits, uint32_t *status) {
+                                                         uint32_t cache_set_bits, TableArgs wt, uint32_t *status) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t bar;
     Classifier<LK> C;
     C.init(t, smem, &bar, status);
+    Classifier<LK_INTERVAL_GLOBAL> W;
+    if (WATCH) W.attach(wt, nullptr);
     const uint64_t pol = policy_evict_first();
-    uint32_t cc[4] = {0, 0, 0, 0}, oor[2] = {0, 0};
+    uint32_t cc[4] = {0, 0, 0, 0}, oor[2] = {0, 0}, flt = 0;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (!AGG) {
         for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < r.g.quads; q += stride) {
             Quad Q;
             load_quad<true, LK != LK_CLASS_IN, true, LK == LK_CLASS_IN>(r, q, pol, Q);
+            watch_filter<WATCH>(W, Q, flt);
             classify_quad<LK>(C, Q);
             combine_quad(h, Q, cc, oor, [&](uint32_t key, uint32_t c, uint64_t s) {
                 gadd(h, key & 1u, key >> 1, c, s);
             });
         }
         flush_counters(h.stats, cc, oor, true);
+        if (WATCH) flush_filtered(h.stats, flt);
         return;
     }
     // hot-key cache after the staged table
@@ -87,6 +118,7 @@ __global__ void __launch_bounds__(256, 3) k_fused_atomic(RecArgs r, TableArgs t,
          q0 += stride) {
         Quad Q;
         load_quad<true, LK != LK_CLASS_IN, true, LK == LK_CLASS_IN>(r, q0 + lane, pol, Q);
+        watch_filter<WATCH>(W, Q, flt);
         classify_quad<LK>(C, Q);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -110,6 +142,7 @@ __global__ void __launch_bounds__(256, 3) k_fused_atomic(RecArgs r, TableArgs t,
         if (c) gadd(h, hc.keys[i] & 1u, hc.keys[i] >> 1, c, (uint64_t)hc.hi[i] << 32 | hc.lo[i]);
     }
     flush_counters(h.stats, cc, oor, true);
+    if (WATCH) flush_filtered(h.stats, flt);
 }
 
 // ---------------------------------------------------------------------------
@@ -313,29 +346,32 @@ cudaError_t run_discriminate(int lk, const RecArgs &r, const TableArgs &t, uint6
 }
 
 cudaError_t run_fused_atomic(int lk, bool agg, const RecArgs &r, const TableArgs &t,
-                             const HistArgs &h, uint32_t cache_set_bits, const LaunchCfg &c) {
+                             const HistArgs &h, uint32_t cache_set_bits, const LaunchCfg &c,
+                             const TableArgs *watch) {
     int grid = 0;
     cudaError_t e;
-#define SINET_ATOM(L, A)                                                                        \
-    if (lk == L && agg == A) {                                                                  \
+    const TableArgs none{};
+#define SINET_ATOM(L, A, WA)                                                                    \
+    if (lk == L && agg == A && (watch != nullptr) == WA) {                                      \
         size_t smem = ((Classifier<L>::smem_bytes(t) + 15u) & ~15u) +                           \
                       (A ? (size_t)HotCache::kSlotBytes * (HotCache::kWays << cache_set_bits) : 0ull);                 \
-        if ((e = launch(k_fused_atomic<L, A>, smem, c, grid)) != cudaSuccess) return e;         \
-        k_fused_atomic<L, A><<<grid, c.block, smem, c.stream>>>(r, t, h, cache_set_bits, c.status); \
+        if ((e = launch(k_fused_atomic<L, A, WA>, smem, c, grid)) != cudaSuccess) return e;     \
+        k_fused_atomic<L, A, WA><<<grid, c.block, smem, c.stream>>>(r, t, h, cache_set_bits,     \
+                                                                   WA ? *watch : none, c.status); \
         return cudaGetLastError();                                                              \
     }
-    SINET_ATOM(LK_INTERVAL, true)
-    SINET_ATOM(LK_INTERVAL, false)
-    SINET_ATOM(LK_TOGGLE1, true)
-    SINET_ATOM(LK_TOGGLE1, false)
-    SINET_ATOM(LK_TOGGLE2, true)
-    SINET_ATOM(LK_TOGGLE2, false)
-    SINET_ATOM(LK_PML, true)
-    SINET_ATOM(LK_PML, false)
-    SINET_ATOM(LK_INTERVAL_GLOBAL, true)
-    SINET_ATOM(LK_INTERVAL_GLOBAL, false)
-    SINET_ATOM(LK_CLASS_IN, true)
-    SINET_ATOM(LK_CLASS_IN, false)
+#define SINET_ATOM2(L, WA) SINET_ATOM(L, true, WA) SINET_ATOM(L, false, WA)
+    SINET_ATOM2(LK_INTERVAL, false)
+    SINET_ATOM2(LK_TOGGLE1, false)
+    SINET_ATOM2(LK_TOGGLE2, false)
+    SINET_ATOM2(LK_PML, false)
+    SINET_ATOM2(LK_INTERVAL_GLOBAL, false)
+    SINET_ATOM2(LK_CLASS_IN, false)
+    SINET_ATOM2(LK_INTERVAL, true)
+    SINET_ATOM2(LK_TOGGLE1, true)
+    SINET_ATOM2(LK_TOGGLE2, true)
+    SINET_ATOM2(LK_INTERVAL_GLOBAL, true)
+#undef SINET_ATOM2
 #undef SINET_ATOM
     return cudaErrorInvalidValue;
 }

@@ -27,8 +27,11 @@ cudaError_t run_discriminate(int lk, const RecArgs &r, const TableArgs &t, uint6
 
 // Fused discriminate + histogram with global atomics (warp-aggregated or not).
 // `cache_set_bits`: log2 of the sets of the per-CTA hot-key cache (4 ways each).
+// `watch` (optional): only records with src or dst in this list are counted
+// and binned; the others count in stats[6].
 cudaError_t run_fused_atomic(int lk, bool agg, const RecArgs &r, const TableArgs &t,
-                             const HistArgs &h, uint32_t cache_set_bits, const LaunchCfg &c);
+                             const HistArgs &h, uint32_t cache_set_bits, const LaunchCfg &c,
+                             const TableArgs *watch = nullptr);
 
 // Fused discriminate + histogram with shared-memory bin tiles.
 cudaError_t run_fused_tile(int lk, const RecArgs &r, const TableArgs &t, const HistArgs &h,

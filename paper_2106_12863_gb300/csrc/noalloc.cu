@@ -73,6 +73,7 @@ extern "C" sinet_status sinet_discriminate_histogram_noalloc(
         return SINET_ERR_INVALID_ARG;
     const int lk = pick_lookup(t, p->lookup, &st);
     if (st != SINET_OK) return st;
+    if (p->watch) return SINET_ERR_UNSUPPORTED;
     HistArgs h = make_hist(p, o);
     if (n * (h.two_dir ? 2ull : 1ull) >= 0xFFFFFFF0ull) return SINET_ERR_BUDGET;
     const SortPlan plan = plan_sort_reduce(n, h.n_bins, h.two_dir);

@@ -464,6 +464,19 @@ sinet_status sinet_server_export(sinet_server *s, uint32_t tenant, uint32_t *h_c
     return SINET_OK;
 }
 
+sinet_status sinet_server_import(sinet_server *s, uint32_t tenant, const uint32_t *h_count, const uint64_t *h_bytes,
+                                 const uint64_t *h_stats) {
+    if (!s || tenant >= s->tenants.size() || !h_count || !h_bytes || !h_stats) return SINET_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);  // no launch starts meanwhile
+    const Tenant &t = s->tenants[tenant];
+    const uint64_t nb = t.params.n_bins;
+    SINET_CUDA(cudaStreamSynchronize(s->compute_stream));
+    SINET_CUDA(cudaMemcpy(t.out.count[0], h_count, 8 * nb, cudaMemcpyHostToDevice));
+    SINET_CUDA(cudaMemcpy(t.out.bytes[0], h_bytes, 16 * nb, cudaMemcpyHostToDevice));
+    SINET_CUDA(cudaMemcpy(t.out.stats, h_stats, 64, cudaMemcpyHostToDevice));
+    return SINET_OK;
+}
+
 sinet_status sinet_server_stats(sinet_server *s, int reset, sinet_server_counters *st) {
     if (!s || !st) return SINET_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);

@@ -50,7 +50,8 @@ class HistParamsC(ctypes.Structure):
                 ("n_bins", ctypes.c_uint64), ("policy", ctypes.c_uint8 * 4),
                 ("accumulate", ctypes.c_int32), ("strategy", ctypes.c_int32),
                 ("lookup", ctypes.c_int32), ("hints", ctypes.c_uint32),
-                ("tile_bins", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
+                ("tile_bins", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("watch", ctypes.c_void_p)]
 
 
 class HistOutC(ctypes.Structure):
@@ -134,6 +135,7 @@ def load():
         "sinet_server_drain": (ctypes.c_int, [_P, u32]),
         "sinet_server_tenant_output": (ctypes.c_int, [_P, u32, ctypes.POINTER(HistOutC)]),
         "sinet_server_export": (ctypes.c_int, [_P, u32, _P, _P, _P]),
+        "sinet_server_import": (ctypes.c_int, [_P, u32, _P, _P, _P]),
         "sinet_server_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ServerCountersC)]),
         "sinet_server_destroy": (ctypes.c_int, [_P]),
         "sinet_default_params": (None, [ctypes.POINTER(HistParamsC), u64, u64, u64]),
@@ -363,6 +365,7 @@ class HistParams:
     hints: int = 0
     tile_bins: int = 0
     block_threads: int = 0
+    watch: object = None  # PrefixTable: only records with src or dst in it are binned
 
     def c(self) -> HistParamsC:
         p = HistParamsC()
@@ -373,6 +376,7 @@ class HistParams:
         p.strategy = STRATEGIES[self.strategy] if isinstance(self.strategy, str) else self.strategy
         p.lookup = LOOKUPS[self.lookup] if isinstance(self.lookup, str) else self.lookup
         p.hints, p.tile_bins, p.block_threads = self.hints, self.tile_bins, self.block_threads
+        p.watch = self.watch.handle if self.watch is not None else None
         return p
 
 
@@ -537,6 +541,15 @@ class Server:
         _check(load().sinet_server_export(self.handle, tenant, c.ctypes.data, b.ctypes.data,
                                           st.ctypes.data), "sinet_server_export")
         return {"count": c, "bytes": b, "stats": st}
+
+    def import_(self, tenant: int, hist: dict):
+        """Replace a tenant's resident histogram with {"count", "bytes", "stats"} host arrays."""
+        c = np.ascontiguousarray(hist["count"], np.uint32)
+        b = np.ascontiguousarray(hist["bytes"], np.uint64)
+        st = np.ascontiguousarray(hist["stats"], np.uint64)
+        assert c.shape == (2, self.n_bins[tenant]) and b.shape == c.shape and st.shape == (8,)
+        _check(load().sinet_server_import(self.handle, tenant, c.ctypes.data, b.ctypes.data,
+                                          st.ctypes.data), "sinet_server_import")
 
     def stats(self, reset: bool = False) -> dict:
         c = ServerCountersC()

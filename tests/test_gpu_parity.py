@@ -280,3 +280,41 @@ def test_accumulate_and_wrap(orc, strategy):
 def test_device_status_is_clean_after_runs():
     torch.cuda.synchronize()
     assert sinet.sinet_device_status() == 0
+
+
+# ---------------------------------------------------------------------------
+# Watch list: only records with src or dst in a second list are binned
+
+
+def _watch_list(rec, seed, hosts=300, prefixes=4):
+    rng = np.random.default_rng(seed)
+    h = np.unique(np.concatenate([rng.choice(rec["src"], hosts // 2), rng.choice(rec["dst"], hosts // 2)]))
+    pre = rng.integers(0, 2 ** 32, prefixes, dtype=np.uint64).astype(np.uint32) & np.uint32(0xFFFF0000)
+    net = np.concatenate([h, pre]).astype(np.uint32)
+    ln = np.concatenate([np.full(len(h), 32, np.uint8), np.full(len(pre), 16, np.uint8)])
+    return net, ln
+
+
+@pytest.mark.parametrize("strategy", ["auto", "global_atomic", "atomic_noagg", "atomic_cell"])
+@pytest.mark.parametrize("key", ["tiny", "heavy"])
+def test_watch_filter(orc, key, strategy):
+    w, net, ln, rec = _workload(key, 400_003)
+    wnet, wln = _watch_list(rec, 3)
+    want = orc.discriminate_histogram_watch(net, ln, wnet, wln, rec, w.t0, w.bin_width, w.n_bins)
+    assert 0 < int(want["stats"][6]) < len(rec["ts"])
+    got = run_fused(sinet.PrefixTable(net, ln), to_dev(rec),
+                    sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy=strategy,
+                                     watch=sinet.PrefixTable(wnet, wln)))
+    assert_hist_equal(got, want, f"{key} watch {strategy}")
+
+
+def test_watch_filter_refused_where_not_run(orc):
+    w, net, ln, rec = _workload("tiny", 10_000)
+    d = to_dev(rec)
+    t, wt = sinet.PrefixTable(net, ln), sinet.PrefixTable(*_watch_list(rec, 4))
+    out = sinet.Histogram(w.n_bins)
+    for s in ("priv_tile", "smem_full", "sort_reduce"):
+        with pytest.raises(sinet.SinetError) as e:
+            sinet.discriminate_histogram(t, d["ts"], d["src"], d["dst"], d["bytes"],
+                                         sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy=s, watch=wt), out)
+        assert e.value.status == 8

@@ -155,3 +155,29 @@ def test_serving_admission_and_timeouts(stream_):
         assert s2.stats()["requests_done"] == 2
     s2.close()
     assert n > 0
+
+
+def test_serving_checkpoint_round_trip(orc, stream_):
+    """Export a tenant, import it into a fresh server, keep serving there: the
+    result equals serving everything on one server (and the oracle)."""
+    tables, data = stream_
+    want = _want(orc, tables, data)
+    half = len(data) // 2
+    a, _ta = _server(tables, budget=64 << 20, per_launch=8)
+    for t, rec in data[:half]:
+        a.wait(a.submit(t, rec["ts"], rec["src"], rec["dst"], rec["bytes"]))
+    a.drain()
+    snap = [a.export(i) for i in range(len(WIDTHS))]
+    a.close()
+    b, _tb = _server(tables, budget=64 << 20, per_launch=8)
+    for i, h in enumerate(snap):
+        b.import_(i, h)
+        back = b.export(i)
+        for k in ("stats", "count", "bytes"):
+            assert np.array_equal(back[k], h[k]), f"tenant {i} {k} round trip"
+    ks = [b.submit(t, rec["ts"], rec["src"], rec["dst"], rec["bytes"]) for t, rec in data[half:]]
+    for k in ks:
+        b.wait(k)
+    b.drain()
+    _check(b, want)
+    b.close()

@@ -276,10 +276,38 @@ def check_sampled_bins(o, seed=9):
     assert np.array_equal(b, h["bytes"][:, keep.astype(np.int64)])
 
 
+def check_watch_filter(o, seed=13):
+    """The watch filter against pins outside the oracle: a /0 list keeps every
+    record; an empty list drops every record into stats[6]; a list of /32
+    hosts keeps exactly the records numpy's isin selects."""
+    wl = gen.scaled(gen.WORKLOADS["tiny"], 20_000)
+    net, ln = gen.make_table(wl.table, wl.seed)
+    rec = gen.make_records(wl.records, wl.seed, net, ln)
+    full = o.discriminate_histogram(net, ln, rec, 0, 60_000, 60)
+    every = o.discriminate_histogram_watch(net, ln, np.array([0], np.uint32), np.array([0], np.uint8), rec,
+                                           0, 60_000, 60)
+    for k in ("count", "bytes", "stats"):
+        assert np.array_equal(every[k], full[k])
+    none = o.discriminate_histogram_watch(net, ln, np.zeros(0, np.uint32), np.zeros(0, np.uint8), rec,
+                                          0, 60_000, 60)
+    assert int(none["stats"][6]) == len(rec["ts"]) and not none["count"].any() and not none["stats"][:6].any()
+    rng = np.random.default_rng(seed)
+    hosts = np.unique(np.concatenate([rng.choice(rec["src"], 150), rng.choice(rec["dst"], 150),
+                                      rng.integers(0, 2 ** 32, 50, dtype=np.uint64).astype(np.uint32)]))
+    watched = o.discriminate_histogram_watch(net, ln, hosts, np.full(len(hosts), 32, np.uint8), rec,
+                                             0, 60_000, 60)
+    keep = np.isin(rec["src"], hosts) | np.isin(rec["dst"], hosts)
+    sub = o.discriminate_histogram(net, ln, {k: v[keep] for k, v in rec.items()}, 0, 60_000, 60)
+    for k in ("count", "bytes"):
+        assert np.array_equal(watched[k], sub[k])
+    assert np.array_equal(watched["stats"][:6], sub["stats"][:6])
+    assert int(watched["stats"][6]) == int((~keep).sum()) > 0 and keep.sum() > 0
+
+
 CHECKS = [check_bitmask_golden, check_membership_golden, check_membership_ipaddress,
           check_membership_brute_force, check_class_bits, check_histogram_golden,
           check_histogram_numpy, check_brute_force_pipeline, check_invariants_generated,
-          check_count_wrap_and_wide_bytes, check_sampled_bins]
+          check_count_wrap_and_wide_bytes, check_sampled_bins, check_watch_filter]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=lambda c: c.__name__)
