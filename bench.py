@@ -70,6 +70,29 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's value (the job's time): an all-reduce MAX when a
+    process group is up, else x."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed, over the slowest rank's time."""
+    return world * units_per_rank * steps / (total_ms / 1e3)
+
+
+def rank_seed(base: int, rank: int, stride: int = 1) -> int:
+    """Weak scaling: each rank draws its own workload (different seed, same shape)."""
+    return base + stride * rank
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -293,7 +316,7 @@ def run_batch_bench(args):
     import paper_2106_12863_gb300 as sinet
 
     sinet.load()
-    plan = gen.batch_slices(n_slices=args.slices, seed=gen.BASE_SEED + 4 + 1000 * rank,
+    plan = gen.batch_slices(n_slices=args.slices, seed=rank_seed(gen.BASE_SEED + 4, rank, 1000),
                             scale=args.scale)
     n_tot = sum(sp.n for sp in plan)
     bins_tot = sum(sp.n_bins for sp in plan)
@@ -359,17 +382,14 @@ def run_batch_bench(args):
     clk = clocks.stop()
     total_ms = t_begin.elapsed_time(t_end)
     graph_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t_ = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t_.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
     st = stats.cpu().numpy().view(np.uint64)
     for i, sp in enumerate(plan):
         assert int(st[i, :4].sum()) == sp.n, f"slice {i}: class counts do not sum to its records"
     ref_stats = st.copy()
 
-    result = {"metric": METRIC, "value": world * n_tot * args.steps / (total_ms / 1e3), "unit": UNIT,
+    result = {"metric": METRIC, "value": job_rate(n_tot, world, args.steps, total_ms), "unit": UNIT,
               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
               "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "u32/u64",
@@ -539,7 +559,7 @@ def run_serve_bench(args):
 
     sinet.load()
     specs, reqs = gen.serving_plan(n_tenants=args.tenants, n_requests=3 * args.requests,
-                                   seed=gen.BASE_SEED + 5 + 1000 * rank, cap=args.request_cap)
+                                   seed=rank_seed(gen.BASE_SEED + 5, rank, 1000), cap=args.request_cap)
     tg = time.perf_counter()
     tables, pools = [], []
     cap = max(r.n for r in reqs)
@@ -688,7 +708,7 @@ def main():
 
     w = workload(args, rank)
     n = w.records.n
-    seed = w.seed + rank  # weak scaling: every rank processes its own day
+    seed = rank_seed(w.seed, rank)  # weak scaling: every rank processes its own day
     net, ln = gen.make_table(w.table, w.seed)
     # records generated straight into pinned host memory, then made resident
     h = {"ts": torch.empty(n, dtype=torch.int64, pin_memory=True),
@@ -775,12 +795,9 @@ def main():
     total_ms = t_begin.elapsed_time(t_end)
     kern_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
     zero_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms / 1e3)
+    value = job_rate(n, world, args.steps, total_ms)
     stats = out.stats.cpu().numpy().view(np.uint64)
     # invariant spot check on the last step: every record classified once
     assert int(stats[:4].sum()) == n, "class counts do not sum to the record count"
