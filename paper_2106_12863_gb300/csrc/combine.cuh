@@ -30,14 +30,18 @@ struct HotCache {
         int way = k4.x == key ? 0 : k4.y == key ? 1 : k4.z == key ? 2 : k4.w == key ? 3 : -1;
         if (way < 0) {
             const uint32_t cur[4] = {k4.x, k4.y, k4.z, k4.w};
+            bool tried = false;
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 if (way < 0 && cur[w] == kNoKey) {
+                    tried = true;
                     const uint32_t old = atomicCAS(kp + w, kNoKey, key);
                     if (old == kNoKey || old == key) way = w;
                 }
             }
-            if (way < 0) {  // a racing claim may have taken another way for this key
+            // a claim lost to a racing lane may have put this key in another
+            // way; a full set (the common miss once warm) tried no claim
+            if (way < 0 && tried) {
 #pragma unroll
                 for (int w = 0; w < 4; ++w)
                     if (way < 0 && *reinterpret_cast<volatile uint32_t *>(kp + w) == key) way = w;
