@@ -236,19 +236,8 @@ __device__ __forceinline__ uint32_t bin_quad(const HistArgs &h, const Quad &Q, u
 }
 
 // Direction bits of a record from its class; a routed record outside the
-// window is counted in oor[] per direction and routes nowhere.
-__device__ __forceinline__ uint32_t dirs_of(const HistArgs &h, uint32_t cls, bool in_window,
-                                            uint32_t oor[2]) {
-    const uint32_t dirs = (h.policy >> (8 * cls)) & 3u;
-    if (!in_window) {
-        oor[0] += dirs & 1u;
-        oor[1] += dirs >> 1;
-        return 0u;
-    }
-    return dirs;
-}
-
-// dirs_of with the out-of-window counts in a packed word (16 bits per direction).
+// window routes nowhere and is counted per direction in a packed word (16
+// bits per direction).
 __device__ __forceinline__ uint32_t dirs_of_packed(const HistArgs &h, uint32_t cls, bool in_window,
                                                    uint32_t &oorp) {
     const uint32_t dirs = (h.policy >> (8 * cls)) & 3u;

@@ -46,6 +46,25 @@ def test_every_declared_symbol_is_exported():
     assert not missing, missing
 
 
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    """include/sinet.h is a plain C header: it compiles as C11 (pedantic) and C++17."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    src = tmp_path / "use.c"
+    src.write_text('#include "sinet.h"\n'
+                   "int main(void) { sinet_hist_params p; sinet_default_params(&p, 0, 1, 10);\n"
+                   "  sinet_batch_slice b; sinet_server_config c; (void)b; (void)c;\n"
+                   "  return (int)p.n_bins - 10; }\n")
+    inc = os.path.join(ROOT, "include")
+    for cmd in (["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only"],
+                ["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-x", "c++"]):
+        r = subprocess.run(cmd + ["-I", inc, str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
 def test_version_and_status_strings():
     assert sinet.sinet_version() >= 0x000100
     L = sinet.load()
