@@ -939,6 +939,27 @@ def main():
         kept = n - int(out.stats.cpu().numpy().view(np.uint64)[6])
         post["watch_877_hosts"] = {"ms": ms, "sessions_per_s": n / (ms / 1e3), "kept": kept}
         watch.close()
+
+        # the split entry points: Algorithm 1 alone (class bytes out), then the
+        # histogram of those classes (8 + 1 and 12 + 1 bytes per record read)
+        cls = torch.empty(n, dtype=torch.uint8, device=dev)
+        hp = sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy="priv_tile", hints=hints)
+        for name, fn, per_rec in (
+                ("discriminate", lambda: sinet.discriminate(table, d["src"], d["dst"], cls), 9),
+                ("histogram_from_classes", lambda: sinet.histogram(d["ts"], d["bytes"], cls, hp, out), 13)):
+            fn()
+            torch.cuda.synchronize()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for _ in range(5):
+                fn()
+            p1.record(stream)
+            torch.cuda.synchronize()
+            ms = p0.elapsed_time(p1) / 5
+            extra = BIN_BYTES * w.n_bins if name == "histogram_from_classes" else 0
+            post[name] = {"ms": ms, "sessions_per_s": n / (ms / 1e3),
+                          "algorithmic_GBs": (per_rec * n + extra) / (ms / 1e3) / 1e9}
+        del cls
         result["post"] = post
         del sp_bin, sp_c, sp_b
 
