@@ -222,3 +222,31 @@ def test_batch_ready_word_set_by_a_copy_on_another_stream(orc):
     for i, c in enumerate(cases):
         assert_hist_equal(c.out.to_numpy(), c.want(orc), f"slice {i}")
     b.close()
+
+
+def test_batch_more_slices_than_shared_starts(orc):
+    """Over 1,024 slices the work-item starts are searched in global memory
+    instead of shared memory; every slice still matches the oracle."""
+    w = gen.WORKLOADS["tiny"]
+    net, ln = gen.make_table(w.table, w.seed)
+    rec = gen.make_records(gen.scaled(w, 1_500 * 700).records, w.seed + 7, net, ln)
+    table = sinet.PrefixTable(net, ln)
+    dev = to_dev(rec)
+    slices, outs, spans = [], [], []
+    rng = np.random.default_rng(5)
+    for i in range(1_500):
+        a, b_ = 700 * i, 700 * i + int(rng.integers(0, 701))  # 0..700 records, some empty
+        nb = int(rng.integers(1, 5000))
+        bw = int(rng.choice([1, 10, 1000]))
+        out = sinet.Histogram(nb, zero=False)
+        outs.append(out)
+        spans.append((a, b_, nb, bw))
+        slices.append((table, dev["ts"][a:b_], dev["src"][a:b_], dev["dst"][a:b_], dev["bytes"][a:b_],
+                       sinet.HistParams(0, bw, nb, strategy=("global_atomic", "atomic_noagg", "auto")[i % 3]), out))
+    batch = sinet.Batch(slices)
+    batch.run()
+    torch.cuda.synchronize()
+    for i, (a, b_, nb, bw) in enumerate(spans):
+        part = {k: v[a:b_] for k, v in rec.items()}
+        assert_hist_equal(outs[i].to_numpy(), orc.discriminate_histogram(net, ln, part, 0, bw, nb), f"slice {i}")
+    batch.close()
