@@ -246,8 +246,16 @@ struct ToggleView {
                     for (uint32_t k = 1; k < nb; ++k) x ^= parity_bits(bp[k], off);
                 }
             } else {
-                x = parity_bits(blocks[d[i] & 0x7FFFu], off) ^ d[i];
-                if (NB == 2) x ^= parity_bits(blocks[(d[i] >> 15) & 0x7FFFu], off);
+                // block 0 is all padding, and four equal differences XOR to
+                // zero, so a pure bucket (or an unused second index) needs no
+                // load: skipping it saves the shared-memory wavefronts
+                x = d[i];
+                const uint32_t b1 = d[i] & 0x7FFFu;
+                if (b1) x ^= parity_bits(blocks[b1], off);
+                if (NB == 2) {
+                    const uint32_t b2 = (d[i] >> 15) & 0x7FFFu;
+                    if (b2) x ^= parity_bits(blocks[b2], off);
+                }
             }
             in[i] = x >> 31;
         }
