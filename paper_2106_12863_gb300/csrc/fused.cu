@@ -183,21 +183,30 @@ __global__ void __launch_bounds__(1024) k_fused_tile(RecArgs r, TableArgs t, His
     const uint64_t qpc = (uint64_t)blockDim.x * ta.iters;
     const uint64_t n_chunks = (r.g.quads + qpc - 1) / qpc;
     const uint32_t lane = threadIdx.x & 31;
+    // thread 0 places each chunk's tile from the chunk's first timestamp,
+    // loaded one chunk ahead so the CTA does not wait on it at the barrier
+    uint64_t ts_first = 0;
+    if (!ta.full && threadIdx.x == 0 && blockIdx.x < n_chunks) {
+        int64_t i0 = quad_base(r.g, (uint64_t)blockIdx.x * qpc);
+        ts_first = r.ts[i0 < 0 ? 0 : i0];
+    }
     __syncthreads();
 
     for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         uint32_t base = 0;
         if (!ta.full) {
             if (threadIdx.x == 0) {
-                int64_t i0 = quad_base(r.g, ch * qpc);
-                if (i0 < 0) i0 = 0;
                 uint32_t b = 0;
-                const uint64_t rel = r.ts[i0] - h.t0;
+                const uint64_t rel = ts_first - h.t0;
                 if (rel < h.span) {
                     b = h.w_is_one ? (uint32_t)rel : (uint32_t)divide(rel, h.div);
                     b = b > ta.margin ? b - ta.margin : 0u;
                 }
                 s_base = b;
+                if (ch + gridDim.x < n_chunks) {
+                    const int64_t i1 = quad_base(r.g, (ch + gridDim.x) * qpc);
+                    ts_first = r.ts[i1 < 0 ? 0 : i1];
+                }
             }
             __syncthreads();
             base = s_base;
