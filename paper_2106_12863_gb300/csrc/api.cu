@@ -236,7 +236,9 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
             ta.iters = (uint32_t)(2048 / ct.block);
         } else {
             // default: as many bins as let two CTAs share an SM (at most
-            // 4,096), and chunks of about two records per tile bin
+            // 4,096), and chunks of about three records per tile bin (fewer,
+            // longer chunks amortise the per-chunk flush; much longer ones
+            // span more bins than the tile holds where records are sparse)
             uint32_t T = p->tile_bins ? p->tile_bins : std::min<uint32_t>(4096, tile_capacity_pair(ds, tsm));
             if (T > cap) T = cap;
             T &= ~255u;
@@ -244,7 +246,7 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
             ta.tile_bins = T;
             ta.full = 0;
             ta.margin = T / 6;
-            ta.iters = (uint32_t)std::max<uint64_t>(1, (2ull * T) / (4ull * ct.block));
+            ta.iters = (uint32_t)std::max<uint64_t>(1, (3ull * T) / (4ull * ct.block));
         }
         // a chunk stays within 65,535 records: a tile entry counts in 16 bits
         while ((uint64_t)ct.block * 4 * ta.iters > 65535 && ta.iters > 1) ta.iters--;
