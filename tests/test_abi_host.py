@@ -290,14 +290,20 @@ def _toggle_lookup(img, lay, addrs):
         assert np.all(b < 2 ** 31)
         par = ((off[:, None] >= b + np.uint64(1)).sum(axis=1) & 1).astype(np.uint8)
         state ^= np.where(use, par, 0).astype(np.uint8)
-    # the kernels' form: bit 31 of desc XOR every (stored - off) mod 2^32
+    # the kernels' form: bit 31 of desc XOR every (stored - off) mod 2^32;
+    # forms 1 and 2 skip block index 0 (all padding: its four equal
+    # differences XOR to zero), so check that skipping it changes nothing
+    assert np.all(blocks[0] == 0x7FFFFFFF)
     x = d.copy()
+    x_skip = d.copy()
     for ix in idx:
         use = ix >= 0
         b = blocks[np.where(use, ix, 0)].astype(np.uint64)
         diff = (b - off[:, None] + np.uint64(1 << 32)) & np.uint64(0xFFFFFFFF)
         v = diff[:, 0] ^ diff[:, 1] ^ diff[:, 2] ^ diff[:, 3]
         x ^= np.where(use, v, np.uint64(0))
+        x_skip ^= np.where(use & ((ix > 0) if form != 0 else use), v, np.uint64(0))
+    assert np.array_equal(x, x_skip)
     assert np.array_equal(((x >> np.uint64(31)) & np.uint64(1)).astype(np.uint8), state)
     return state
 
@@ -358,3 +364,30 @@ def test_too_dense_bucket_uses_global_intervals():
     ln = np.full(80, 32, np.uint8)
     img, lay = sinet.sinet_prefix_table_image(net, ln)
     assert lay["iv_fits_smem"] == 0
+
+
+def test_toggle_lookup_property(orc):
+    """Property test (hypothesis): any list of up to 60 prefixes, host bits
+    set, lengths /0-/32 with duplicates and nesting; the compiled image's
+    lookup replayed on the host equals the oracle's loop over every entry at
+    every prefix edge, its neighbours and random addresses."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    entry = st.tuples(st.integers(0, 2 ** 32 - 1), st.integers(0, 32))
+
+    @hyp.settings(max_examples=120, deadline=None, derandomize=True)
+    @hyp.given(st.lists(entry, min_size=1, max_size=60), st.integers(0, 2 ** 31))
+    def check(entries, seed):
+        net = np.array([e[0] for e in entries], np.uint32)
+        ln = np.array([e[1] for e in entries], np.uint8)
+        addrs = _edge_addrs(net, ln, random.Random(seed), extra=64)
+        img, lay = sinet.sinet_prefix_table_image(net, ln)
+        want = (orc.classify(net, ln, addrs, np.zeros_like(addrs)) & 1).astype(np.uint8)
+        if lay["iv_fits_smem"]:
+            assert np.array_equal(_toggle_lookup(img, lay, addrs), want)
+        t = sinet.sinet_compile_prefix_table(net, ln)
+        got = _member_index(t["lo"], t["hi"], t["index"], t["index_bits"], addrs)
+        assert np.array_equal(got, want.astype(bool))
+
+    check()
