@@ -383,6 +383,7 @@ sinet_status sinet_parse_cidr(const char *text, uint32_t *net, uint8_t *len) {
 
 sinet_status sinet_build_prefix_table(const uint32_t *h_net, const uint8_t *h_len, uint32_t n,
                                       sinet_stream_t stream, sinet_prefix_table **out) {
+    SINET_TRACE();
     if (!out) return SINET_ERR_INVALID_ARG;
     *out = nullptr;
     sinet_prefix_table *t = new (std::nothrow) sinet_prefix_table();
@@ -441,6 +442,7 @@ sinet_status sinet_destroy_prefix_table(sinet_prefix_table *t) {
 sinet_status sinet_discriminate(const sinet_prefix_table *t, const uint32_t *d_src, const uint32_t *d_dst,
                                 uint64_t n, uint8_t *d_class, uint64_t *d_class_counts, int32_t lookup,
                                 sinet_stream_t stream) {
+    SINET_TRACE();
     if (!t || !d_class_counts || !aligned(d_class_counts, 8)) return SINET_ERR_INVALID_ARG;
     if (n > kMaxN) return SINET_ERR_INVALID_ARG;
     if (n && (!d_src || !d_dst || !aligned(d_src, 4) || !aligned(d_dst, 4))) return SINET_ERR_INVALID_ARG;
@@ -467,6 +469,7 @@ sinet_status sinet_discriminate(const sinet_prefix_table *t, const uint32_t *d_s
 
 sinet_status sinet_histogram(const uint64_t *d_ts, const uint32_t *d_bytes, const uint8_t *d_class, uint64_t n,
                              const sinet_hist_params *p, const sinet_hist_out *o, sinet_stream_t stream) {
+    SINET_TRACE();
     sinet_status st = check_params(p);
     if (st != SINET_OK) return st;
     if ((st = check_out(o)) != SINET_OK) return st;
@@ -486,6 +489,7 @@ sinet_status sinet_discriminate_histogram(const sinet_prefix_table *t, const uin
                                           const uint32_t *d_dst, const uint32_t *d_bytes, uint64_t n,
                                           const sinet_hist_params *p, const sinet_hist_out *o,
                                           sinet_stream_t stream) {
+    SINET_TRACE();
     if (!t) return SINET_ERR_INVALID_ARG;
     sinet_status st = check_params(p);
     if (st != SINET_OK) return st;

@@ -2,6 +2,8 @@
 #pragma once
 #include <initializer_list>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 #include "table_host.h"
 
@@ -34,6 +36,16 @@ sinet_status cuda_fail(cudaError_t e);
         cudaError_t e_ = (x);                                  \
         if (e_ != cudaSuccess) return ::sinet::cuda_fail(e_);  \
     } while (0)
+
+// A profiler-visible range around a C-ABI call (NVTX; it costs nothing when
+// no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define SINET_TRACE() ::sinet::TraceRange sinet_trace_range_(__func__)
 
 struct Stream {
     const void *p;

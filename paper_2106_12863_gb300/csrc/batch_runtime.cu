@@ -394,6 +394,7 @@ extern "C" {
 
 sinet_status sinet_batch_create(const sinet_batch_slice *slices, uint32_t n_slices, uint32_t flags,
                                 sinet_stream_t stream, sinet_batch **out) {
+    SINET_TRACE();
     if (!out) return SINET_ERR_INVALID_ARG;
     *out = nullptr;
     if (!slices || n_slices == 0 || n_slices > 65536 || (flags & ~SINET_BATCH_AUTOTUNE))
@@ -450,6 +451,7 @@ sinet_status sinet_batch_create(const sinet_batch_slice *slices, uint32_t n_slic
 }
 
 sinet_status sinet_batch_run(sinet_batch *b, sinet_stream_t stream) {
+    SINET_TRACE();
     if (!b) return SINET_ERR_INVALID_ARG;
     int dev = 0;
     SINET_CUDA(cudaGetDevice(&dev));

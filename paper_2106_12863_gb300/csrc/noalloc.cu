@@ -63,6 +63,7 @@ extern "C" sinet_status sinet_discriminate_histogram_noalloc(
     const sinet_prefix_table *t, const uint64_t *d_ts, const uint32_t *d_src, const uint32_t *d_dst,
     const uint32_t *d_bytes, uint64_t n, const sinet_hist_params *p, const sinet_hist_out *o,
     sinet_stream_t stream) {
+    SINET_TRACE();
     if (!t) return SINET_ERR_INVALID_ARG;
     sinet_status st = check_params(p);
     if (st != SINET_OK) return st;

@@ -193,6 +193,7 @@ extern "C" {
 
 sinet_status sinet_histogram_rollup(const sinet_hist_out *in, uint64_t n_bins, uint64_t factor, int accumulate,
                                     const sinet_hist_out *out, sinet_stream_t stream) {
+    SINET_TRACE();
     if (!out_arrays_ok(in) || !out_arrays_ok(out) || n_bins == 0 || n_bins > 0x7FFFFFFFull || factor == 0)
         return SINET_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
@@ -217,6 +218,7 @@ sinet_status sinet_histogram_rollup(const sinet_hist_out *in, uint64_t n_bins, u
 sinet_status sinet_histogram_sparse(const sinet_hist_out *in, uint64_t n_bins, uint32_t *d_bin, uint32_t *d_count0,
                                     uint32_t *d_count1, uint64_t *d_bytes0, uint64_t *d_bytes1, uint64_t cap,
                                     uint64_t *d_n_out, sinet_stream_t stream) {
+    SINET_TRACE();
     if (!out_arrays_ok(in) || n_bins == 0 || n_bins > 0x7FFFFFFFull || !d_n_out || !aligned(d_n_out, 8))
         return SINET_ERR_INVALID_ARG;
     if (cap && (!d_bin || !d_count0 || !d_count1 || !d_bytes0 || !d_bytes1 || !aligned(d_bin, 4) ||

@@ -251,6 +251,7 @@ void worker_main(sinet_server *s) {
             }
         }
         if (!s->launch_active && !s->ready.empty() && s->error == SINET_OK) {
+            TraceRange range("sinet_server_launch");
             const size_t take = std::min<size_t>(s->ready.size(), s->cfg.max_requests_per_launch);
             std::vector<Request *> batch(s->ready.begin(), s->ready.begin() + take);
             s->ready.erase(s->ready.begin(), s->ready.begin() + take);
@@ -298,6 +299,7 @@ extern "C" {
 
 sinet_status sinet_server_create(const sinet_server_config *cfg, const sinet_tenant *tenants, uint32_t n_tenants,
                                  sinet_server **out) {
+    SINET_TRACE();
     if (!out) return SINET_ERR_INVALID_ARG;
     *out = nullptr;
     if (!cfg || !tenants || n_tenants == 0 || cfg->inflight_budget_bytes < (1u << 20) ||
@@ -453,6 +455,7 @@ sinet_status sinet_server_tenant_output(sinet_server *s, uint32_t tenant, sinet_
 
 sinet_status sinet_server_export(sinet_server *s, uint32_t tenant, uint32_t *h_count, uint64_t *h_bytes,
                                  uint64_t *h_stats) {
+    SINET_TRACE();
     if (!s || tenant >= s->tenants.size() || !h_count || !h_bytes || !h_stats) return SINET_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);  // no launch starts meanwhile
     const Tenant &t = s->tenants[tenant];
@@ -466,6 +469,7 @@ sinet_status sinet_server_export(sinet_server *s, uint32_t tenant, uint32_t *h_c
 
 sinet_status sinet_server_import(sinet_server *s, uint32_t tenant, const uint32_t *h_count, const uint64_t *h_bytes,
                                  const uint64_t *h_stats) {
+    SINET_TRACE();
     if (!s || tenant >= s->tenants.size() || !h_count || !h_bytes || !h_stats) return SINET_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);  // no launch starts meanwhile
     const Tenant &t = s->tenants[tenant];
