@@ -93,6 +93,15 @@ def rank_seed(base: int, rank: int, stride: int = 1) -> int:
     return base + stride * rank
 
 
+def data_digest(tensors, sample: int = 1 << 20) -> str:
+    """SHA-256 over the first `sample` elements of each host buffer (a
+    reproducibility stamp of the generated input)."""
+    h = hashlib.sha256()
+    for t in tensors:
+        h.update(t[:sample].numpy().tobytes())
+    return h.hexdigest()[:16]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -408,7 +417,8 @@ def run_batch_bench(args):
                         "strategies": strat_count, "tune_s": round(t_tune, 2),
                         "l2": f"inputs larger than L2 ({RECORD_BYTES * n_tot / 1e9:.1f} GB of records)",
                         "policy": "exclusive", "parallelism": f"replicas x{world} (weak)",
-                        "gen_s": round(t_gen, 1)}
+                        "gen_s": round(t_gen, 1), "seed": rank_seed(gen.BASE_SEED + 4, rank, 1000),
+                        "data_sha256_prefix": data_digest([h["ts"], h["src"], h["dst"], h["bytes"]])}
     result["clocks"] = clk
 
     def per_slice(strategy):
@@ -825,7 +835,8 @@ def main():
                         "n_bins": w.n_bins, "bin_width_ms": w.bin_width, "strategy": strategy,
                         "tune_ms": tune, "l2": f"inputs larger than L2 ({RECORD_BYTES * n / 1e9:.1f} GB of records)",
                         "policy": "exclusive", "parallelism": f"replicas x{world} (weak)",
-                        "gen_s": round(t_gen, 1)}
+                        "gen_s": round(t_gen, 1), "seed": seed,
+                        "data_sha256_prefix": data_digest([h["ts"], h["src"], h["dst"], h["bytes"]])}
     result["clocks"] = clk
 
     # the plain path (paper's structure) on the same data
