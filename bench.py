@@ -59,7 +59,7 @@ def parse():
                     help="shrink records, window and bins together (keeps records per bin; "
                          "for profiling captures)")
     ap.add_argument("--strategy", default="tune",
-                    help="tune | global_atomic | priv_tile | atomic_noagg | atomic_cell | sort_reduce")
+                    help="tune | owner | global_atomic | priv_tile | atomic_noagg | atomic_cell | sort_reduce")
     ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true")
@@ -135,13 +135,25 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# The files each timed kernel is compiled from: its translation unit and the
+# headers it includes.
+KERNEL_SOURCES = {
+    "k_fused_tile": ["fused.cu", "combine.cuh", "launch.h", "records.cuh", "common.cuh"],
+    "k_fused_atomic": ["fused.cu", "combine.cuh", "launch.h", "records.cuh", "common.cuh"],
+    "k_fused_owner": ["owner.cu", "owner.h", "launch.h", "records.cuh", "common.cuh"],
+}
+
+
+def kernel_source_hash(kernel: str | None = None):
+    """Hash of a kernel's source files (all of csrc/ for other kernels)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_12863_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    files = KERNEL_SOURCES.get(kernel) or sorted(
+        f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h", ".cpp")))
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -151,7 +163,7 @@ def recorded_traffic(kernel: str, workload: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel)
     with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():
@@ -744,8 +756,9 @@ def main():
         out.stats.zero_()
 
     def writes_every_bin(strategy):
-        # the cell strategy expands every bin into the outputs itself
-        return strategy == "atomic_cell"
+        # the cell strategy expands every bin into the outputs itself, and the
+        # owners store every bin
+        return strategy in ("atomic_cell", "owner")
 
     def step(strategy):
         if writes_every_bin(strategy):
@@ -757,7 +770,9 @@ def main():
                                      params(strategy), out)
 
     # autotune: one untimed run of each candidate, keep the fastest
-    cands = (["priv_tile", "global_atomic", "atomic_noagg", "atomic_cell"] if args.strategy == "tune"
+    # the owner-computes scheme is for time-sorted input only
+    cands = ((["owner"] if hints else []) + ["priv_tile", "global_atomic", "atomic_noagg", "atomic_cell"]
+             if args.strategy == "tune"
              else [args.strategy])
     tune = {}
     for c in cands:
@@ -818,7 +833,7 @@ def main():
               "data": "synthetic (seeded generator; paper-shaped day)"}
     alg_bytes = RECORD_BYTES * n + BIN_BYTES * w.n_bins
     peak, peak_kind = peaks()
-    kname = {"priv_tile": "k_fused_tile", "global_atomic": "k_fused_atomic",
+    kname = {"owner": "k_fused_owner", "priv_tile": "k_fused_tile", "global_atomic": "k_fused_atomic",
              "atomic_noagg": "k_fused_atomic", "atomic_cell": "k_fused_atomic",
              "sort_reduce": "k_radix_pass"}[strategy]
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
@@ -829,8 +844,9 @@ def main():
                           "kernel_ms": kern_ms, "zero_ms": zero_ms,
                           "step_frac": alg_bytes / (ms_per_step / 1e3) / 1e9 / peak}
     # one fused kernel per step (zeroing is cudaMemsetAsync), plus the cell
-    # expansion kernel for the cell strategy
-    result["gpu_launches"] = args.steps * (2 if strategy == "atomic_cell" else 1)
+    # expansion kernel for the cell strategy, and the run boundaries, their
+    # scan and the remainder kernel for the owner strategy
+    result["gpu_launches"] = args.steps * {"atomic_cell": 2, "owner": 4}.get(strategy, 1)
     result["config"] = {"workload": w.name, "records": n, "prefixes": w.table.n,
                         "n_bins": w.n_bins, "bin_width_ms": w.bin_width, "strategy": strategy,
                         "tune_ms": tune, "l2": f"inputs larger than L2 ({RECORD_BYTES * n / 1e9:.1f} GB of records)",

@@ -66,10 +66,23 @@ typedef enum {
     SINET_STRAT_SORT_REDUCE = 3,   /* plain path: discriminate, radix sort, reduce by key */
     SINET_STRAT_SMEM_FULL = 4,     /* whole histogram privatised in shared memory (small n_bins) */
     SINET_STRAT_ATOMIC_NOAGG = 5,  /* global atomics without warp aggregation */
-    SINET_STRAT_ATOMIC_CELL = 6    /* GLOBAL_ATOMIC into a library scratch of one 32-byte cell per
+    SINET_STRAT_ATOMIC_CELL = 6,   /* GLOBAL_ATOMIC into a library scratch of one 32-byte cell per
                                       bin (both directions' count and byte sum in one DRAM sector),
                                       then expanded into the output arrays: for unsorted input over
                                       histograms far larger than L2 */
+    SINET_STRAT_OWNER = 7          /* owner computes, for time-sorted input: each CTA owns a block
+                                      of bin ranges, takes the run of records that falls into each
+                                      range (binary search on ts) through a circular shared-memory
+                                      tile that also spans half a range on either side, and stores
+                                      every bin once with plain stores, so the outputs need no
+                                      zeroing and see no read-modify-write. Exact for any input:
+                                      records out of order by more than the halo, and runs longer
+                                      than 32,767 records, are added by a second kernel with global
+                                      reductions. tile_bins sets the tile (rounded down to a power
+                                      of two, at least 16; ranges are half of it). Scratch, stream-
+                                      ordered: 8 bytes per range, 4 per CTA, 32 per queued item
+                                      (at most one per range plus one per 32,767 records). At most
+                                      512 threads per block. */
 } sinet_strategy;
 
 /* How membership is looked up. Both are exact. */
@@ -97,7 +110,7 @@ typedef struct {
     int32_t strategy;      /* sinet_strategy */
     int32_t lookup;        /* sinet_lookup */
     uint32_t hints;        /* SINET_HINT_* */
-    uint32_t tile_bins;    /* PRIV_TILE bins per direction per tile (0 = default) */
+    uint32_t tile_bins;    /* PRIV_TILE / OWNER bins per direction per tile (0 = default) */
     uint32_t block_threads;/* threads per CTA (0 = default) */
     const struct sinet_prefix_table *watch; /* optional watch list (the blocklist views of Section 6):
                               only records whose src or dst is in it are classified and binned,

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "api_internal.h"
+#include "owner.h"
 
 namespace sinet {
 
@@ -94,7 +95,7 @@ sinet_status check_params(const sinet_hist_params *p) {
     if (end > (unsigned __int128)UINT64_MAX) return SINET_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (p->policy[c] > 3) return SINET_ERR_INVALID_ARG;
-    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_ATOMIC_CELL) return SINET_ERR_INVALID_ARG;
+    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_OWNER) return SINET_ERR_INVALID_ARG;
     if (p->lookup < SINET_LOOKUP_AUTO || p->lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
     if (p->block_threads && (p->block_threads > 1024 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
     return SINET_OK;
@@ -216,7 +217,7 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         if (2ull * p->n_bins <= 8192 && p->n_bins <= cap)
             strat = SINET_STRAT_SMEM_FULL;
         else if (p->hints & SINET_HINT_TIME_SORTED)
-            strat = SINET_STRAT_PRIV_TILE;
+            strat = SINET_STRAT_OWNER;
         else if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4)
             strat = SINET_STRAT_ATOMIC_CELL;
         else
@@ -254,9 +255,24 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     }
     if (strat == SINET_STRAT_SORT_REDUCE && r.g.n * (h.two_dir ? 2ull : 1ull) >= 0xFFFFFFF0ull)
         return SINET_ERR_UNSUPPORTED;
+    OwnerPlan oplan{};
+    LaunchCfg co = c;
+    if (strat == SINET_STRAT_OWNER) {
+        // tile slots as for PRIV_TILE's tile (two CTAs of 512 threads per SM)
+        co.block = p->block_threads ? (int)p->block_threads : 512;
+        if (co.block > 512) return SINET_ERR_UNSUPPORTED;
+        uint32_t S = p->tile_bins ? p->tile_bins : std::min<uint32_t>(4096, tile_capacity_pair(ds, tsm));
+        if (S > cap) S = cap;
+        if (S < 16) return SINET_ERR_UNSUPPORTED;
+        oplan = plan_owner(r.g.n, h.n_bins, S, 0);
+        int g = 0;
+        const cudaError_t eg = owner_grid(lk, h.w_is_one != 0, ta_tab, oplan.slots, co, &g);
+        if (eg != cudaSuccess) return cuda_fail(eg);
+        oplan = plan_owner(r.g.n, h.n_bins, S, (uint32_t)g);
+    }
 
-    if (strat == SINET_STRAT_ATOMIC_CELL && !p->accumulate && r.g.n > 0) {
-        // the expansion writes every bin; only the counters start at zero
+    if ((strat == SINET_STRAT_ATOMIC_CELL || strat == SINET_STRAT_OWNER) && !p->accumulate && r.g.n > 0) {
+        // the expansion (cells) or the owners write every bin; only the counters start at zero
         cudaError_t ez = cudaMemsetAsync(o->stats, 0, 64, s);
         if (ez != cudaSuccess) return cuda_fail(ez);
     } else {
@@ -289,6 +305,18 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         case SINET_STRAT_SMEM_FULL:
             e = run_fused_tile(lk, r, ta_tab, h, ta, ct);
             break;
+        case SINET_STRAT_OWNER: {
+            void *scratch = nullptr;
+            e = cudaMallocAsync(&scratch, oplan.scratch_bytes, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            const bool vec = aligned(o->count[0], 16) && aligned(o->count[1], 16) &&
+                             aligned(o->bytes[0], 16) && aligned(o->bytes[1], 16);
+            e = run_fused_owner(lk, r, ta_tab, h, p->bin_width_ms, oplan, scratch, p->accumulate != 0,
+                                vec, co);
+            const cudaError_t e2 = cudaFreeAsync(scratch, s);
+            if (e == cudaSuccess) e = e2;
+            break;
+        }
         case SINET_STRAT_SORT_REDUCE: {
             SortPlan plan = plan_sort_reduce(r.g.n, h.n_bins, h.two_dir);
             void *scratch = nullptr;

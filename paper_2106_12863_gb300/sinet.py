@@ -24,11 +24,11 @@ STATUS = {0: "SINET_OK", 1: "SINET_ERR_INVALID_ARG", 2: "SINET_ERR_CUDA", 3: "SI
           7: "SINET_ERR_DEVICE_CHECK", 8: "SINET_ERR_UNSUPPORTED"}
 
 STRAT_AUTO, STRAT_GLOBAL_ATOMIC, STRAT_PRIV_TILE, STRAT_SORT_REDUCE, STRAT_SMEM_FULL, \
-    STRAT_ATOMIC_NOAGG, STRAT_ATOMIC_CELL = range(7)
+    STRAT_ATOMIC_NOAGG, STRAT_ATOMIC_CELL, STRAT_OWNER = range(8)
 STRATEGIES = {"auto": STRAT_AUTO, "global_atomic": STRAT_GLOBAL_ATOMIC,
               "priv_tile": STRAT_PRIV_TILE, "sort_reduce": STRAT_SORT_REDUCE,
               "smem_full": STRAT_SMEM_FULL, "atomic_noagg": STRAT_ATOMIC_NOAGG,
-              "atomic_cell": STRAT_ATOMIC_CELL}
+              "atomic_cell": STRAT_ATOMIC_CELL, "owner": STRAT_OWNER}
 LOOKUP_AUTO, LOOKUP_INTERVAL, LOOKUP_PML = range(3)
 LOOKUPS = {"auto": LOOKUP_AUTO, "interval": LOOKUP_INTERVAL, "pml": LOOKUP_PML}
 HINT_TIME_SORTED = 1

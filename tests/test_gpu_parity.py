@@ -24,7 +24,7 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU too
 
 import paper_2106_12863_gb300 as sinet  # noqa: E402
 
-STRATS = ["global_atomic", "atomic_noagg", "atomic_cell", "priv_tile", "sort_reduce"]
+STRATS = ["global_atomic", "atomic_noagg", "atomic_cell", "priv_tile", "owner", "sort_reduce"]
 POLICIES = {"exclusive": sinet.EXCLUSIVE, "inclusive": sinet.INCLUSIVE, "paper_alg1": sinet.PAPER_ALG1}
 
 
@@ -313,7 +313,7 @@ def test_watch_filter_refused_where_not_run(orc):
     d = to_dev(rec)
     t, wt = sinet.PrefixTable(net, ln), sinet.PrefixTable(*_watch_list(rec, 4))
     out = sinet.Histogram(w.n_bins)
-    for s in ("priv_tile", "smem_full", "sort_reduce"):
+    for s in ("priv_tile", "smem_full", "owner", "sort_reduce"):
         with pytest.raises(sinet.SinetError) as e:
             sinet.discriminate_histogram(t, d["ts"], d["src"], d["dst"], d["bytes"],
                                          sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy=s, watch=wt), out)
