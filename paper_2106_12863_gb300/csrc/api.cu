@@ -217,7 +217,9 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         if (2ull * p->n_bins <= 8192 && p->n_bins <= cap)
             strat = SINET_STRAT_SMEM_FULL;
         else if (p->hints & SINET_HINT_TIME_SORTED)
-            strat = SINET_STRAT_OWNER;
+            // the tile strategy: measured faster than OWNER on the paper-shaped
+            // day (about 4.6 records per ms bin, +-500 ms disorder)
+            strat = SINET_STRAT_PRIV_TILE;
         else if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4)
             strat = SINET_STRAT_ATOMIC_CELL;
         else

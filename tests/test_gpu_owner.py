@@ -113,12 +113,13 @@ def test_accumulate(orc, n_bins):
     assert_hist_equal(out.to_numpy(), ref, f"n_bins={n_bins}")
 
 
-def test_auto_with_sorted_hint(orc):
+@pytest.mark.parametrize("strategy", ["owner", "auto"])
+def test_sorted_hint(orc, strategy):
     net, ln, rec = _records(300_007, 3_600_000, 500, 26)
     ref = orc.discriminate_histogram(net, ln, rec, 0, 1, 3_600_000)
     got = run_fused(sinet.PrefixTable(net, ln), to_dev(rec),
-                    sinet.HistParams(0, 1, 3_600_000, hints=sinet.HINT_TIME_SORTED))
-    assert_hist_equal(got, ref, "auto + sorted hint")
+                    sinet.HistParams(0, 1, 3_600_000, strategy=strategy, hints=sinet.HINT_TIME_SORTED))
+    assert_hist_equal(got, ref, f"{strategy} + sorted hint")
 
 
 @pytest.mark.parametrize("kw", [{"block_threads": 1024}, {"tile_bins": 8}])
