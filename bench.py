@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -144,16 +145,24 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments or layout: a comment edit leaves it as is."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(kernel: str | None = None):
-    """Hash of a kernel's source files (all of csrc/ for other kernels)."""
+    """Hash of a kernel's source code (all of csrc/ for other kernels),
+    comments and whitespace excluded."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_12863_gb300", "csrc")
     files = KERNEL_SOURCES.get(kernel) or sorted(
         f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h", ".cpp")))
     for f in files:
-        with open(os.path.join(csrc, f), "rb") as fh:
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             h.update(f.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -147,13 +147,13 @@ __global__ void __launch_bounds__(256, 3) k_fused_atomic(RecArgs r, TableArgs t,
 
 // ---------------------------------------------------------------------------
 // Shared-memory privatised bins. A CTA takes chunks of blockDim * iters quads
-// (at most 8,192 records); for each chunk it places a tile of `tile_bins`
+// (at most 65,535 records); for each chunk it places a tile of `tile_bins`
 // bins per direction just below the chunk's first record (time-sorted input
 // keeps the chunk inside it). A tile entry is two 32-bit words updated with
 // native shared atomics: the low 32 bits of the byte sum, and a high word
 // holding the record count in its upper 16 bits and the byte sum's bits
-// 32-47 in its lower 16 (a bin of one chunk holds at most 8,192 records,
-// whose bytes sum below 2^45). The touched part of the tile is flushed with
+// 32-47 in its lower 16 (a bin of one chunk holds at most 65,535 records,
+// whose bytes sum below 2^48). The touched part of the tile is flushed with
 // global atomics after the chunk. Records outside the tile go straight to
 // global atomics. With `full`, the tile is the whole histogram (base 0).
 template <int LK, bool W1>
