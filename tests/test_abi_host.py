@@ -391,3 +391,54 @@ def test_toggle_lookup_property(orc):
         assert np.array_equal(got, want.astype(bool))
 
     check()
+
+
+def test_ctypes_layouts_and_constants_match_the_header(tmp_path):
+    """The binding's ctypes mirrors and constants equal what a C compiler
+    makes of include/sinet.h: every struct's size and field offsets, and
+    every enum and flag value."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    structs = {"sinet_hist_params": sinet.HistParamsC, "sinet_hist_out": sinet.HistOutC,
+               "sinet_batch_slice": sinet.BatchSliceC, "sinet_tenant": sinet.TenantC,
+               "sinet_server_config": sinet.ServerConfigC, "sinet_request_info": sinet.RequestInfoC,
+               "sinet_server_counters": sinet.ServerCountersC}
+    consts = {f"SINET_STRAT_{k.upper()}": v for k, v in sinet.STRATEGIES.items()}
+    consts.update({f"SINET_LOOKUP_{k.upper()}": v for k, v in sinet.LOOKUPS.items()})
+    consts.update({name: code for code, name in sinet.STATUS.items()})
+    consts.update({"SINET_HINT_TIME_SORTED": sinet.HINT_TIME_SORTED, "SINET_BATCH_AUTOTUNE": sinet.BATCH_AUTOTUNE,
+                   "SINET_DIR_OUT": sinet.DIR_OUT, "SINET_DIR_IN": sinet.DIR_IN})
+    # every enum member and flag the header defines has a binding constant
+    import re
+
+    with open(os.path.join(ROOT, "include", "sinet.h")) as f:
+        header = f.read()
+    declared = set(re.findall(r"\b(SINET_(?:STRAT|LOOKUP|ERR)_[A-Z0-9_]+)\s*=", header)) | {"SINET_OK"}
+    declared |= set(re.findall(r"#define (SINET_(?:HINT|DIR|BATCH)_[A-Z0-9_]+)", header))
+    assert declared <= set(consts), sorted(declared - set(consts))
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sinet.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    for name in consts:
+        lines.append(f'  printf("{name} %lld\\n", (long long){name});')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, f"{cname}.{fname}"
+    for name, v in consts.items():
+        assert int(got[name]) == v, name
