@@ -70,7 +70,7 @@ typedef enum {
                                       bin (both directions' count and byte sum in one DRAM sector),
                                       then expanded into the output arrays: for unsorted input over
                                       histograms far larger than L2 */
-    SINET_STRAT_OWNER = 7          /* owner computes, for time-sorted input: each CTA owns a block
+    SINET_STRAT_OWNER = 7,         /* owner computes, for time-sorted input: each CTA owns a block
                                       of bin ranges, takes the run of records that falls into each
                                       range (binary search on ts) through a circular shared-memory
                                       tile that also spans half a range on either side, and stores
@@ -83,6 +83,24 @@ typedef enum {
                                       ordered: 8 bytes per range, 4 per CTA, 32 per queued item
                                       (at most one per range plus one per 32,767 records). At most
                                       512 threads per block. */
+    SINET_STRAT_PARTITION = 8      /* hot/cold partition, for unsorted input over histograms far
+                                      larger than L2 (Section 5's map-reduce with the reduction
+                                      kept on chip): a strided sample of about n / 256 records
+                                      ranks the bins; the most sampled ones (up to 16,384 slots,
+                                      as shared memory allows) are summed in shared memory by
+                                      every CTA; every other routed update is appended as an
+                                      8-byte (bin, direction, bytes) entry to a page of its
+                                      bin range, and a cooperative second kernel sorts the pages
+                                      by owner CTA in place and has each CTA sum its own bins in
+                                      shared memory and store each of them once. The outputs
+                                      need no zeroing and see no read-modify-write. tile_bins, a
+                                      power of two, sets the bins per range (default 2^19; raised
+                                      until there are at most 256 ranges; at most 2^20).
+                                      sinet_discriminate_histogram only, no watch list; at most
+                                      2^32 - 4,096 routed updates and 2^28 bins. Scratch, stream-
+                                      ordered: 16 bytes per routed update plus about 2.5 KB per
+                                      2,048-entry page for its bookkeeping, and 48 MB at most
+                                      for the sample. */
 } sinet_strategy;
 
 /* How membership is looked up. Both are exact. */
@@ -125,7 +143,9 @@ typedef struct {
  *   bytes[d]: uint64[n_bins]  (sum of the records' bytes field)
  *   stats:    uint64[8]       (records per class [0..3], out-of-window records per
  *                              routed direction [4..5], records left out by the watch
- *                              list [6], reserved [7])
+ *                              list [6]; [7]: its low 32 bits carry the device-side
+ *                              status of sinet_discriminate_histogram_noalloc, which
+ *                              clears them at every call; otherwise reserved)
  * A record routed to direction d whose ts lies outside the window is not
  * binned; it is counted in stats[4 + d].
  */
@@ -229,6 +249,17 @@ sinet_status sinet_histogram(const uint64_t *d_ts, const uint32_t *d_bytes, cons
                              sinet_stream_t stream);
 
 /*
+ * The binning step of Section 5 alone: d_bin[i] = (ts[i] - t0) / w for a
+ * record inside the window [t0, t0 + n_bins * w), else 0xFFFFFFFF. The same
+ * device division (an invariant-divisor multiply) as every histogram kernel.
+ *   d_ts   device uint64[n]; d_bin device uint32[n] (caller-owned)
+ * Parameters are checked as for the histogram (w >= 1, 1 <= n_bins < 2^31,
+ * t0 + n_bins * w within uint64); SINET_ERR_INVALID_ARG otherwise.
+ */
+sinet_status sinet_bin(const uint64_t *d_ts, uint64_t n, uint64_t t0_ms, uint64_t bin_width_ms,
+                       uint64_t n_bins, uint32_t *d_bin, sinet_stream_t stream);
+
+/*
  * Fused Algorithm 1 + histogram in one pass over the records (the hot path).
  * p->strategy selects the update scheme (SINET_STRAT_SORT_REDUCE runs the
  * plain discriminate -> radix sort -> reduce-by-key path). Output as in
@@ -263,7 +294,9 @@ sinet_status sinet_discriminate_histogram(const sinet_prefix_table *t, const uin
  * GPU (different streams, no ordering between them) race on it: order them.
  * The array keeps the previous call's contents; the call clears what must
  * start at zero itself. A device-side failure (a bounded wait that ran out)
- * is latched into the low 32 bits of stats[7] as a sinet_status code.
+ * is latched into the low 32 bits of stats[7] as a sinet_status code; every
+ * call clears those 32 bits first (also when accumulating), so they report
+ * this call only.
  * Other arguments, outputs and errors as in sinet_discriminate_histogram.
  */
 sinet_status sinet_discriminate_histogram_noalloc(const sinet_prefix_table *t, const uint64_t *d_ts,

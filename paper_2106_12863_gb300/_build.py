@@ -21,7 +21,7 @@ OBJ_DIR = os.path.join(HERE, "_lib", "obj")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include")]
-UNITS = ["api.cu", "fused.cu", "sort.cu", "noalloc.cu", "batch.cu", "batch_runtime.cu", "server.cu", "post.cu", "owner.cu", "table_host.cpp"]
+UNITS = ["api.cu", "fused.cu", "sort.cu", "noalloc.cu", "batch.cu", "batch_runtime.cu", "server.cu", "post.cu", "owner.cu", "partition.cu", "table_host.cpp"]
 
 
 def _nvcc() -> str:

@@ -7,6 +7,7 @@
 
 #include "api_internal.h"
 #include "owner.h"
+#include "partition.h"
 
 namespace sinet {
 
@@ -95,7 +96,7 @@ sinet_status check_params(const sinet_hist_params *p) {
     if (end > (unsigned __int128)UINT64_MAX) return SINET_ERR_INVALID_ARG;
     for (int c = 0; c < 4; ++c)
         if (p->policy[c] > 3) return SINET_ERR_INVALID_ARG;
-    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_OWNER) return SINET_ERR_INVALID_ARG;
+    if (p->strategy < SINET_STRAT_AUTO || p->strategy > SINET_STRAT_PARTITION) return SINET_ERR_INVALID_ARG;
     if (p->lookup < SINET_LOOKUP_AUTO || p->lookup > SINET_LOOKUP_PML) return SINET_ERR_INVALID_ARG;
     if (p->block_threads && (p->block_threads > 1024 || p->block_threads % 32)) return SINET_ERR_INVALID_ARG;
     return SINET_OK;
@@ -220,8 +221,14 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
             // the tile strategy: measured faster than OWNER on the paper-shaped
             // day (about 4.6 records per ms bin, +-500 ms disorder)
             strat = SINET_STRAT_PRIV_TILE;
-        else if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4)
-            strat = SINET_STRAT_ATOMIC_CELL;
+        else if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4) {
+            // unsorted input over a histogram far beyond L2: the hot/cold
+            // partition where its limits allow, else the cells
+            PartPlan probe{};
+            strat = plan_partition(lk, tsm, r, h, 0, ds->sm_count, ds->smem_optin, &probe) == cudaSuccess
+                        ? SINET_STRAT_PARTITION
+                        : SINET_STRAT_ATOMIC_CELL;
+        }
         else
             strat = SINET_STRAT_GLOBAL_ATOMIC;
     }
@@ -257,6 +264,18 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     }
     if (strat == SINET_STRAT_SORT_REDUCE && r.g.n * (h.two_dir ? 2ull : 1ull) >= 0xFFFFFFF0ull)
         return SINET_ERR_UNSUPPORTED;
+    PartPlan pplan{};
+    if (strat == SINET_STRAT_PARTITION) {
+        if (watch) return SINET_ERR_UNSUPPORTED;
+        uint32_t bb = 0;
+        if (p->tile_bins) {
+            if (p->tile_bins & (p->tile_bins - 1)) return SINET_ERR_INVALID_ARG;
+            while ((1u << bb) < p->tile_bins) ++bb;
+            if (bb > 20) return SINET_ERR_UNSUPPORTED;
+        }
+        if (plan_partition(lk, tsm, r, h, bb, ds->sm_count, ds->smem_optin, &pplan) != cudaSuccess)
+            return SINET_ERR_UNSUPPORTED;
+    }
     OwnerPlan oplan{};
     LaunchCfg co = c;
     if (strat == SINET_STRAT_OWNER) {
@@ -273,8 +292,10 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         oplan = plan_owner(r.g.n, h.n_bins, S, (uint32_t)g);
     }
 
-    if ((strat == SINET_STRAT_ATOMIC_CELL || strat == SINET_STRAT_OWNER) && !p->accumulate && r.g.n > 0) {
-        // the expansion (cells) or the owners write every bin; only the counters start at zero
+    if ((strat == SINET_STRAT_ATOMIC_CELL || strat == SINET_STRAT_OWNER || strat == SINET_STRAT_PARTITION) &&
+        !p->accumulate && r.g.n > 0) {
+        // the expansion (cells), the owners or the cold pass write every bin;
+        // only the counters start at zero
         cudaError_t ez = cudaMemsetAsync(o->stats, 0, 64, s);
         if (ez != cudaSuccess) return cuda_fail(ez);
     } else {
@@ -315,6 +336,15 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
                              aligned(o->bytes[0], 16) && aligned(o->bytes[1], 16);
             e = run_fused_owner(lk, r, ta_tab, h, p->bin_width_ms, oplan, scratch, p->accumulate != 0,
                                 vec, co);
+            const cudaError_t e2 = cudaFreeAsync(scratch, s);
+            if (e == cudaSuccess) e = e2;
+            break;
+        }
+        case SINET_STRAT_PARTITION: {
+            void *scratch = nullptr;
+            e = cudaMallocAsync(&scratch, pplan.scratch_bytes, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            e = run_partition(lk, r, ta_tab, h, pplan, scratch, p->accumulate != 0, c);
             const cudaError_t e2 = cudaFreeAsync(scratch, s);
             if (e == cudaSuccess) e = e2;
             break;
@@ -494,6 +524,29 @@ sinet_status sinet_discriminate(const sinet_prefix_table *t, const uint32_t *d_s
     c.status = ds->status;
     c.sm_count = ds->sm_count;
     SINET_CUDA(run_discriminate(lk, r, t->args, d_class_counts, c));
+    return SINET_OK;
+}
+
+sinet_status sinet_bin(const uint64_t *d_ts, uint64_t n, uint64_t t0_ms, uint64_t bin_width_ms, uint64_t n_bins,
+                       uint32_t *d_bin, sinet_stream_t stream) {
+    SINET_TRACE();
+    sinet_hist_params p;
+    sinet_default_params(&p, t0_ms, bin_width_ms, n_bins);
+    sinet_status st = check_params(&p);
+    if (st != SINET_OK) return st;
+    if (n > kMaxN) return SINET_ERR_INVALID_ARG;
+    if (n && (!d_ts || !d_bin || !aligned(d_ts, 8) || !aligned(d_bin, 4))) return SINET_ERR_INVALID_ARG;
+    if (n == 0) return SINET_OK;
+    DeviceState *ds = nullptr;
+    if ((st = device_state(&ds)) != SINET_OK) return st;
+    HistArgs h{};
+    h.t0 = t0_ms;
+    h.span = n_bins * bin_width_ms;
+    h.div = make_divider(bin_width_ms);
+    LaunchCfg c;
+    c.stream = stream;
+    c.sm_count = ds->sm_count;
+    SINET_CUDA(run_bin(d_ts, n, h, d_bin, c));
     return SINET_OK;
 }
 

@@ -97,8 +97,9 @@ __device__ __forceinline__ void red_add_u64(uint64_t *p, uint64_t v) {
 // ---------------------------------------------------------------------------
 // Bulk (TMA engine, non-tensor) copy of a 16-byte-aligned global region into
 // shared memory, completed on an mbarrier. Called by all threads of the CTA;
-// returns false (and latches SINET_ERR_TIMEOUT) if the copy did not land
-// within the polling bound.
+// returns false in every thread (and latches SINET_ERR_TIMEOUT) if the copy
+// did not land within the polling bound: the caller must then not classify
+// against the shared memory.
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -147,8 +148,9 @@ __device__ inline bool stage_to_smem(void *sdst, const void *gsrc, uint32_t byte
         for (uint32_t it = 0; it < kSpinLimit && !mbar_try_wait(b, 0); ++it) {
         }
     }
-    __syncthreads();
-    return ok;
+    // one answer for the whole CTA: a thread whose polls ran out makes every
+    // thread treat the staged table as absent
+    return __syncthreads_and(ok) != 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256) k_discriminate(RecArgs r, TableArgs t, ui
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t bar;
     Classifier<LK> C;
-    C.init(t, smem, &bar, status);
+    if (!C.init(t, smem, &bar, status)) return;  // table not staged: the status word says so
     const uint64_t pol = policy_evict_first();
     uint32_t cc[4] = {0, 0, 0, 0}, oor[2] = {0, 0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256, 3) k_fused_atomic(RecArgs r, TableArgs t,
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint64_t bar;
     Classifier<LK> C;
-    C.init(t, smem, &bar, status);
+    if (!C.init(t, smem, &bar, status)) return;  // table not staged: the status word says so
     Classifier<LK_INTERVAL_GLOBAL> W;
     if (WATCH) W.attach(wt, nullptr);
     const uint64_t pol = policy_evict_first();
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(1024) k_fused_tile(RecArgs r, TableArgs t, His
     __shared__ uint32_t s_base, s_lo, s_hi;
     __shared__ unsigned long long s_cnt[6];
     Classifier<LK> C;
-    C.init(t, smem, &bar, status);
+    if (!C.init(t, smem, &bar, status)) return;  // table not staged: the status word says so
     const uint32_t T = ta.tile_bins;
     uint32_t *tlo = reinterpret_cast<uint32_t *>(smem + ((Classifier<LK>::smem_bytes(t) + 15u) & ~15u));
     uint32_t *thi = tlo + 2 * T;
@@ -274,6 +274,21 @@ __global__ void __launch_bounds__(1024) k_fused_tile(RecArgs r, TableArgs t, His
     __syncthreads();
     if (threadIdx.x < 6 && s_cnt[threadIdx.x])
         atomicAdd(reinterpret_cast<unsigned long long *>(h.stats) + threadIdx.x, s_cnt[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// Binning alone: the bin of each record, or kNoKey outside the window.
+__global__ void __launch_bounds__(256) k_bin(const uint64_t *ts, uint64_t n, HistArgs h, uint32_t *bin) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t rel = ts[i] - h.t0;
+        bin[i] = rel < h.span ? (uint32_t)divide(rel, h.div) : kNoKey;
+    }
+}
+
+cudaError_t run_bin(const uint64_t *ts, uint64_t n, const HistArgs &h, uint32_t *bin, const LaunchCfg &c) {
+    k_bin<<<8 * c.sm_count, 256, 0, c.stream>>>(ts, n, h, bin);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -21,6 +21,9 @@ struct TileArgs {
     uint32_t full;        // 1: the tile is the whole histogram (base 0)
 };
 
+// The bin of each record ((ts - t0) / w) or 0xFFFFFFFF outside the window.
+cudaError_t run_bin(const uint64_t *ts, uint64_t n, const HistArgs &h, uint32_t *bin, const LaunchCfg &c);
+
 // Algorithm 1 only: class bytes (optional) and class counts.
 cudaError_t run_discriminate(int lk, const RecArgs &r, const TableArgs &t, uint64_t *counts,
                              const LaunchCfg &c);

@@ -82,6 +82,9 @@ extern "C" sinet_status sinet_discriminate_histogram_noalloc(
 
     NoAllocDevice *d = nullptr;
     if ((st = noalloc_setup(&d)) != SINET_OK) return st;
+    // this call's device-side status starts clear, accumulating or not, so a
+    // failure latched by an earlier call is not reported again
+    if (cudaMemsetAsync(o->stats + 7, 0, 4, stream) != cudaSuccess) return SINET_ERR_CUDA;
     if ((st = zero_outputs(p, o, stream)) != SINET_OK) return st;
     if (n == 0) return SINET_OK;
 

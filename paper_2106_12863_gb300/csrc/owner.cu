@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(512, 2) k_fused_owner(RecArgs r, TableArgs t, 
     }
     if (k0 >= k1) return;  // for sorted input the remainder kernel usually ends here
     Classifier<LK> C;
-    C.init(t, smem, &bar, status);
+    if (!C.init(t, smem, &bar, status)) return;  // table not staged: the status word says so
     const uint32_t S = oa.S;
     uint32_t *tlo = reinterpret_cast<uint32_t *>(smem + ((Classifier<LK>::smem_bytes(t) + 15u) & ~15u));
     uint32_t *thi = tlo + 2 * S;

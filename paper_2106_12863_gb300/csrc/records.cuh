@@ -48,10 +48,12 @@ struct Classifier;
 template <int NB>
 struct ToggleClassifier {
     ToggleView<NB> v;
-    __device__ __forceinline__ void init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
+    // false (in every thread of the CTA) when the table did not land
+    __device__ __forceinline__ bool init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
                                          uint32_t *status) {
-        stage_to_smem(smem, t.image, t.iv_bytes, bar, status);
+        const bool ok = stage_to_smem(smem, t.image, t.iv_bytes, bar, status);
         attach(t, smem);
+        return ok;
     }
     // views over an image already staged at `smem`
     __device__ __forceinline__ void attach(const TableArgs &t, const uint8_t *smem) {
@@ -76,12 +78,13 @@ struct Classifier<LK_TOGGLE2> : ToggleClassifier<2> {};
 template <>
 struct Classifier<LK_PML> {
     PmlView v;
-    __device__ __forceinline__ void init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
+    __device__ __forceinline__ bool init(const TableArgs &t, uint8_t *smem, uint64_t *bar,
                                          uint32_t *status) {
-        stage_to_smem(smem, t.image + t.off_nets, t.pml_bytes, bar, status);
+        const bool ok = stage_to_smem(smem, t.image + t.off_nets, t.pml_bytes, bar, status);
         v.nets = reinterpret_cast<const uint32_t *>(smem);
         v.groups = reinterpret_cast<const uint4 *>(smem + (t.off_groups - t.off_nets));
         v.n_groups = t.n_groups;
+        return ok;
     }
     static __host__ __device__ uint32_t smem_bytes(const TableArgs &t) { return t.pml_bytes; }
     template <int N>
@@ -94,8 +97,9 @@ struct Classifier<LK_PML> {
 template <>
 struct Classifier<LK_INTERVAL_GLOBAL> {
     IntervalView<uint32_t> v;
-    __device__ __forceinline__ void init(const TableArgs &t, uint8_t *, uint64_t *, uint32_t *) {
+    __device__ __forceinline__ bool init(const TableArgs &t, uint8_t *, uint64_t *, uint32_t *) {
         attach(t, nullptr);
+        return true;
     }
     __device__ __forceinline__ void attach(const TableArgs &t, const uint8_t *) {
         v.lo = reinterpret_cast<const uint32_t *>(t.image + t.off_lo);
@@ -114,7 +118,7 @@ struct Classifier<LK_INTERVAL_GLOBAL> {
 
 template <>
 struct Classifier<LK_CLASS_IN> {
-    __device__ __forceinline__ void init(const TableArgs &, uint8_t *, uint64_t *, uint32_t *) {}
+    __device__ __forceinline__ bool init(const TableArgs &, uint8_t *, uint64_t *, uint32_t *) { return true; }
     static __host__ __device__ uint32_t smem_bytes(const TableArgs &) { return 0; }
     template <int N>
     __device__ __forceinline__ void in_n(const uint32_t (&)[N], uint32_t (&r)[N]) const {

@@ -93,7 +93,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(RecArgs r, TableArgs t, H
     __shared__ uint32_t s_warp[kEmitThreads / 32];
     __shared__ uint64_t s_tile, s_goff;
     Classifier<LK> C;
-    C.init(t, smem, &bar, status);
+    // a table that did not land leaves this tile's records out (the status
+    // word says so), but the tile still takes part in the look-back chain
+    const bool tab_ok = C.init(t, smem, &bar, status);
     const uint32_t tsm = (Classifier<LK>::smem_bytes(t) + 15u) & ~15u;
     uint32_t *skey = reinterpret_cast<uint32_t *>(smem + tsm);
     const uint32_t cap = kEmitRecords * (h.two_dir ? 2 : 1);
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(RecArgs r, TableArgs t, H
         const uint64_t q = tile * (kEmitThreads * kEmitQuadsPerThread) + (uint64_t)it * kEmitThreads + threadIdx.x;
         Quad Q;
         load_quad<true, LK != LK_CLASS_IN, true, LK == LK_CLASS_IN>(r, q, pol, Q);
+        if (!tab_ok) Q.valid = 0;
         classify_quad<LK>(C, Q);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {

@@ -24,11 +24,12 @@ STATUS = {0: "SINET_OK", 1: "SINET_ERR_INVALID_ARG", 2: "SINET_ERR_CUDA", 3: "SI
           7: "SINET_ERR_DEVICE_CHECK", 8: "SINET_ERR_UNSUPPORTED"}
 
 STRAT_AUTO, STRAT_GLOBAL_ATOMIC, STRAT_PRIV_TILE, STRAT_SORT_REDUCE, STRAT_SMEM_FULL, \
-    STRAT_ATOMIC_NOAGG, STRAT_ATOMIC_CELL, STRAT_OWNER = range(8)
+    STRAT_ATOMIC_NOAGG, STRAT_ATOMIC_CELL, STRAT_OWNER, STRAT_PARTITION = range(9)
 STRATEGIES = {"auto": STRAT_AUTO, "global_atomic": STRAT_GLOBAL_ATOMIC,
               "priv_tile": STRAT_PRIV_TILE, "sort_reduce": STRAT_SORT_REDUCE,
               "smem_full": STRAT_SMEM_FULL, "atomic_noagg": STRAT_ATOMIC_NOAGG,
-              "atomic_cell": STRAT_ATOMIC_CELL, "owner": STRAT_OWNER}
+              "atomic_cell": STRAT_ATOMIC_CELL, "owner": STRAT_OWNER,
+              "partition": STRAT_PARTITION}
 LOOKUP_AUTO, LOOKUP_INTERVAL, LOOKUP_PML = range(3)
 LOOKUPS = {"auto": LOOKUP_AUTO, "interval": LOOKUP_INTERVAL, "pml": LOOKUP_PML}
 HINT_TIME_SORTED = 1
@@ -111,6 +112,7 @@ def load():
         "sinet_build_prefix_table": (ctypes.c_int, [_P, _P, u32, _P, _P]),
         "sinet_destroy_prefix_table": (ctypes.c_int, [_P]),
         "sinet_discriminate": (ctypes.c_int, [_P, _P, _P, u64, _P, _P, i32, _P]),
+        "sinet_bin": (ctypes.c_int, [_P, u64, u64, u64, u64, _P, _P]),
         "sinet_histogram": (ctypes.c_int, [_P, _P, _P, u64, ctypes.POINTER(HistParamsC),
                                            ctypes.POINTER(HistOutC), _P]),
         "sinet_discriminate_histogram": (ctypes.c_int, [_P, _P, _P, _P, _P, u64,
@@ -255,6 +257,11 @@ def sinet_discriminate(table: int, d_src, d_dst, n: int, d_class, d_class_counts
     _check(load().sinet_discriminate(table, _dptr(d_src), _dptr(d_dst), n, _dptr(d_class),
                                      _dptr(d_class_counts), lookup, _stream(stream)),
            "sinet_discriminate")
+
+
+def sinet_bin(d_ts, n: int, t0_ms: int, bin_width_ms: int, n_bins: int, d_bin, stream=None):
+    _check(load().sinet_bin(_dptr(d_ts), n, t0_ms, bin_width_ms, n_bins, _dptr(d_bin), _stream(stream)),
+           "sinet_bin")
 
 
 def sinet_histogram(d_ts, d_bytes, d_class, n: int, params: HistParamsC, out: HistOutC, stream=None):
@@ -421,6 +428,15 @@ def discriminate(table: PrefixTable, src, dst, cls=None, lookup="auto", stream=N
 
 def histogram(ts, nbytes, cls, params: HistParams, out: Histogram, stream=None):
     sinet_histogram(ts, nbytes, cls, ts.numel(), params.c(), out.c(), stream)
+    return out
+
+
+def bin_index(ts, t0_ms: int, bin_width_ms: int, n_bins: int, out=None, stream=None):
+    """Bin of each timestamp (uint32 bits in int32; 0xFFFFFFFF outside the window)."""
+    import torch
+
+    out = out if out is not None else torch.empty(ts.numel(), dtype=torch.int32, device=ts.device)
+    sinet_bin(ts, ts.numel(), t0_ms, bin_width_ms, n_bins, out, stream)
     return out
 
 

@@ -24,7 +24,7 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU too
 
 import paper_2106_12863_gb300 as sinet  # noqa: E402
 
-STRATS = ["global_atomic", "atomic_noagg", "atomic_cell", "priv_tile", "owner", "sort_reduce"]
+STRATS = ["global_atomic", "atomic_noagg", "atomic_cell", "priv_tile", "owner", "sort_reduce", "partition"]
 POLICIES = {"exclusive": sinet.EXCLUSIVE, "inclusive": sinet.INCLUSIVE, "paper_alg1": sinet.PAPER_ALG1}
 
 
@@ -180,12 +180,17 @@ def test_heavy_zipf_slice(orc, strategy):
 def test_histogram_of_classified_records(orc):
     w, net, ln, rec = _workload("tiny", 300_001, seed_shift=2)
     cls = orc.classify(net, ln, rec["src"], rec["dst"])
+    d = to_dev({"ts": rec["ts"], "bytes": rec["bytes"], "cls": cls})
     for strategy in STRATS:
         ref = orc.histogram(rec["ts"], rec["bytes"], cls, 1000, 3, 1_000_000, sinet.INCLUSIVE)
         out = sinet.Histogram(1_000_000)
-        d = to_dev({"ts": rec["ts"], "bytes": rec["bytes"], "cls": cls})
-        sinet.histogram(d["ts"], d["bytes"], d["cls"],
-                        sinet.HistParams(1000, 3, 1_000_000, policy=sinet.INCLUSIVE, strategy=strategy), out)
+        params = sinet.HistParams(1000, 3, 1_000_000, policy=sinet.INCLUSIVE, strategy=strategy)
+        if strategy == "partition":  # fused entry point only
+            with pytest.raises(sinet.SinetError) as e:
+                sinet.histogram(d["ts"], d["bytes"], d["cls"], params, out)
+            assert e.value.status == 8
+            continue
+        sinet.histogram(d["ts"], d["bytes"], d["cls"], params, out)
         torch.cuda.synchronize()
         assert_hist_equal(out.to_numpy(), ref, strategy)
 
@@ -313,7 +318,7 @@ def test_watch_filter_refused_where_not_run(orc):
     d = to_dev(rec)
     t, wt = sinet.PrefixTable(net, ln), sinet.PrefixTable(*_watch_list(rec, 4))
     out = sinet.Histogram(w.n_bins)
-    for s in ("priv_tile", "smem_full", "owner", "sort_reduce"):
+    for s in ("priv_tile", "smem_full", "owner", "sort_reduce", "partition"):
         with pytest.raises(sinet.SinetError) as e:
             sinet.discriminate_histogram(t, d["ts"], d["src"], d["dst"], d["bytes"],
                                          sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy=s, watch=wt), out)
