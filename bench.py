@@ -46,9 +46,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="day", choices=sorted(gen.WORKLOADS) + ["batch", "serve"],
-                    help="day | heavy | tiny: one window; batch: 256 uneven slices in one "
+    ap.add_argument("--workload", default="heavy", choices=sorted(gen.WORKLOADS) + ["batch", "serve"],
+                    help="heavy | day | tiny: one window; batch: 256 uneven slices in one "
                          "persistent launch; serve: the continuous-batching serving loop")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "records", "time"],
+                    help="with N > 1 ranks: replicas (every rank its own workload, weak scaling); "
+                         "records (one workload split by record range, partial histograms merged by "
+                         "an NCCL reduce-scatter inside the timed step; strong); time (one "
+                         "time-sorted workload split by owned bin range, no collective; strong)")
+    ap.add_argument("--no-day", action="store_true",
+                    help="heavy: skip the extra line of figures for the time-sorted 400 M day")
     ap.add_argument("--slices", type=int, default=256, help="batch: number of slices")
     ap.add_argument("--tenants", type=int, default=32, help="serve: tenants")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests per phase")
@@ -60,7 +67,8 @@ def parse():
                     help="shrink records, window and bins together (keeps records per bin; "
                          "for profiling captures)")
     ap.add_argument("--strategy", default="tune",
-                    help="tune | owner | global_atomic | priv_tile | atomic_noagg | atomic_cell | sort_reduce")
+                    help="tune | partition | owner | global_atomic | priv_tile | atomic_noagg | atomic_cell "
+                         "| sort_reduce")
     ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true")
@@ -108,6 +116,38 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def workload_named(name):
+    return gen.WORKLOADS[name]
+
+
+def owned_records(w, net, ln, world, rank, chunk=50_000_000):
+    """Time-range split: the records of workload w whose ts falls in this
+    rank's owned bins (rank 0 also takes the records outside the window),
+    generated chunk by chunk and kept in pinned host memory."""
+    import torch
+
+    from paper_2106_12863_gb300 import shard
+
+    win = shard.Window(w.t0, w.bin_width, w.n_bins).owned(world, rank)
+    lo, hi = win.t0, win.t0 + win.n_bins * win.width
+    end = w.t0 + w.n_bins * w.bin_width
+    parts = {k: [] for k in ("ts", "src", "dst", "bytes")}
+    for first in range(0, w.records.n, chunk):
+        r = gen.make_records(w.records, w.seed, net, ln, first=first, n=min(chunk, w.records.n - first))
+        keep = (r["ts"] >= np.uint64(lo)) & (r["ts"] < np.uint64(hi))
+        if rank == 0:
+            keep |= (r["ts"] < np.uint64(w.t0)) | (r["ts"] >= np.uint64(end))
+        for k in parts:
+            parts[k].append(r[k][keep])
+    out = {}
+    for k, dt in (("ts", torch.int64), ("src", torch.int32), ("dst", torch.int32), ("bytes", torch.int32)):
+        a = np.concatenate(parts[k])
+        t = torch.empty(len(a), dtype=dt, pin_memory=True)
+        t.numpy()[:] = a.view(t.numpy().dtype)
+        out[k] = t
+    return out
 
 
 def workload(args, rank):
@@ -738,25 +778,65 @@ def main():
     sinet.load()  # fails loudly without the CUDA library
 
     w = workload(args, rank)
-    n = w.records.n
-    seed = rank_seed(w.seed, rank)  # weak scaling: every rank processes its own day
+    result = run_window_bench(args, w, rank, world, dev, extras=True)
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    # the paper-shaped time-sorted day as a second, smaller line of figures
+    if args.workload == "heavy" and not args.no_day and not args.records and args.scale == 1.0:
+        torch.cuda.empty_cache()
+        day = run_window_bench(args, workload_named("day"), rank, world, dev, extras=False)
+        result["day"] = {k: day[k] for k in ("value", "unit", "ms_per_step", "roofline", "config",
+                                              "plain_sort_reduce", "fused_vs_plain", "clocks") if k in day}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_window_bench(args, w, rank, world, dev, extras: bool):
+    """One window workload (tiny, day or heavy): tune, time K steps, the plain
+    path, and (with extras) the end-to-end pipeline and the post-processing."""
+    import torch
+
+    import paper_2106_12863_gb300 as sinet
+
+    from paper_2106_12863_gb300 import shard
+
+    mode = args.shard if world > 1 else "single"
+    n_total = w.records.n
     net, ln = gen.make_table(w.table, w.seed)
-    # records generated straight into pinned host memory, then made resident
-    h = {"ts": torch.empty(n, dtype=torch.int64, pin_memory=True),
-         "src": torch.empty(n, dtype=torch.int32, pin_memory=True),
-         "dst": torch.empty(n, dtype=torch.int32, pin_memory=True),
-         "bytes": torch.empty(n, dtype=torch.int32, pin_memory=True)}
     tg = time.perf_counter()
-    gen.fill_records(w.records, seed, net, ln, 0, n, h["ts"], h["src"], h["dst"], h["bytes"])
+    if mode == "time":
+        # this rank owns bins [lo, hi) and is given the records that fall there
+        if w.records.ts_kind != "diurnal":
+            raise SystemExit("--shard time needs a time-sorted workload (day)")
+        h, seed = owned_records(w, net, ln, world, rank), w.seed
+        win = shard.Window(w.t0, w.bin_width, w.n_bins).owned(world, rank)
+        n = int(h["ts"].numel())
+    else:
+        if mode == "records":  # this rank's share of one workload
+            first, last = shard.record_range(n_total, world, rank)
+            seed = w.seed
+        else:  # replicas: every rank processes its own day (weak scaling)
+            first, last = 0, n_total
+            seed = rank_seed(w.seed, rank)
+        n = last - first
+        # records generated straight into pinned host memory, then made resident
+        h = {"ts": torch.empty(n, dtype=torch.int64, pin_memory=True),
+             "src": torch.empty(n, dtype=torch.int32, pin_memory=True),
+             "dst": torch.empty(n, dtype=torch.int32, pin_memory=True),
+             "bytes": torch.empty(n, dtype=torch.int32, pin_memory=True)}
+        gen.fill_records(w.records, seed, net, ln, first, n, h["ts"], h["src"], h["dst"], h["bytes"])
+        win = shard.Window(w.t0, w.bin_width, w.n_bins)
     t_gen = time.perf_counter() - tg
     d = {k: v.to(dev) for k, v in h.items()}
     table = sinet.PrefixTable(net, ln)
-    out = sinet.Histogram(w.n_bins, dev, zero=False)
+    out = sinet.Histogram(win.n_bins, dev, zero=False)
     stream = torch.cuda.current_stream(dev)
     hints = sinet.HINT_TIME_SORTED if w.records.ts_kind == "diurnal" else 0
 
     def params(strategy, accumulate=True):
-        return sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy=strategy, hints=hints,
+        return sinet.HistParams(win.t0, win.width, win.n_bins, strategy=strategy, hints=hints,
                                 accumulate=accumulate)
 
     def zero():
@@ -765,9 +845,9 @@ def main():
         out.stats.zero_()
 
     def writes_every_bin(strategy):
-        # the cell strategy expands every bin into the outputs itself, and the
-        # owners store every bin
-        return strategy in ("atomic_cell", "owner")
+        # the cell strategy expands every bin into the outputs itself; the
+        # owners and the partition's cold pass store every bin
+        return strategy in ("atomic_cell", "owner", "partition")
 
     def step(strategy):
         if writes_every_bin(strategy):
@@ -778,11 +858,16 @@ def main():
         sinet.discriminate_histogram(table, d["ts"], d["src"], d["dst"], d["bytes"],
                                      params(strategy), out)
 
-    # autotune: one untimed run of each candidate, keep the fastest
-    # the owner-computes scheme is for time-sorted input only
-    cands = ((["owner"] if hints else []) + ["priv_tile", "global_atomic", "atomic_noagg", "atomic_cell"]
-             if args.strategy == "tune"
-             else [args.strategy])
+    # autotune: one untimed run of each candidate, keep the fastest. The
+    # owner-computes scheme and the tile are for time-sorted input; unsorted
+    # input over a histogram far beyond L2 leaves the partition, the cells
+    # and the combining atomics (plain atomics there take ~10x longer)
+    if args.strategy != "tune":
+        cands = [args.strategy]
+    elif hints:
+        cands = ["owner", "priv_tile", "global_atomic", "atomic_cell", "partition"]
+    else:
+        cands = ["partition", "atomic_cell", "global_atomic"]
     tune = {}
     for c in cands:
         step(c)
@@ -801,7 +886,7 @@ def main():
     # timed region: K steps, zero + fused kernel, events on the launching stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index)
     time.sleep(0.3)
     if world > 1:
         torch.distributed.barrier()
@@ -819,6 +904,8 @@ def main():
         b.record(stream)
         sinet.discriminate_histogram(table, d["ts"], d["src"], d["dst"], d["bytes"],
                                      params(strategy, accumulate=not own), out)
+        if mode == "records":  # merge the ranks' partial histograms (each keeps its bin slice)
+            shard.merge(out.count, out.bytes, out.stats, scatter=True)
         c.record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -831,35 +918,51 @@ def main():
     zero_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
     total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = job_rate(n, world, args.steps, total_ms)
+    if mode in ("records", "time"):  # one workload over all ranks (strong scaling)
+        value = n_total * args.steps / (total_ms / 1e3)
+    else:
+        value = job_rate(n, world, args.steps, total_ms)
     stats = out.stats.cpu().numpy().view(np.uint64)
     # invariant spot check on the last step: every record classified once
-    assert int(stats[:4].sum()) == n, "class counts do not sum to the record count"
+    # (after a record-range merge the counters hold every rank's records)
+    assert int(stats[:4].sum()) == (n_total if mode == "records" else n), \
+        "class counts do not sum to the record count"
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
-              "data": "synthetic (seeded generator; paper-shaped day)"}
-    alg_bytes = RECORD_BYTES * n + BIN_BYTES * w.n_bins
+              "scaling": "strong" if mode in ("records", "time") else "weak", "vs_baseline": None,
+              "dtype": "u32/u64", "data": f"synthetic (seeded generator; {w.name})"}
+    alg_bytes = RECORD_BYTES * n + BIN_BYTES * win.n_bins
     peak, peak_kind = peaks()
     kname = {"owner": "k_fused_owner", "priv_tile": "k_fused_tile", "global_atomic": "k_fused_atomic",
              "atomic_noagg": "k_fused_atomic", "atomic_cell": "k_fused_atomic",
-             "sort_reduce": "k_radix_pass"}[strategy]
-    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+             "partition": "k_part_main", "sort_reduce": "k_radix_pass"}[strategy]
+    # the fraction counts everything a step needs (the zeroing that the tile
+    # and atomic schemes require included): algorithmic bytes over the step
+    achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
     result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                           "frac": achieved / peak, "traffic": recorded_traffic(kname, w.name),
                           "kernel": kname, "peak_kind": peak_kind,
                           "algorithmic_bytes_per_launch": alg_bytes,
-                          "kernel_ms": kern_ms, "zero_ms": zero_ms,
-                          "step_frac": alg_bytes / (ms_per_step / 1e3) / 1e9 / peak}
-    # one fused kernel per step (zeroing is cudaMemsetAsync), plus the cell
-    # expansion kernel for the cell strategy, and the run boundaries, their
-    # scan and the remainder kernel for the owner strategy
-    result["gpu_launches"] = args.steps * {"atomic_cell": 2, "owner": 4}.get(strategy, 1)
+                          "step_ms": ms_per_step, "call_ms": kern_ms, "zero_ms": zero_ms,
+                          "call_frac": alg_bytes / (kern_ms / 1e3) / 1e9 / peak,
+                          "timed": "whole step (CUDA events on the launching stream): "
+                                   + ("the library call" if own else "output zeroing + the library call")}
+    # kernels per step: one fused kernel (zeroing is cudaMemsetAsync), plus
+    # the cell expansion for the cell strategy; the run boundaries, their scan
+    # and the remainder for the owner strategy; sample, levels, candidates,
+    # hot table, main pass, three page-grouping kernels, cold pass and hot
+    # totals for the partition
+    result["gpu_launches"] = args.steps * {"atomic_cell": 2, "owner": 4, "partition": 10}.get(strategy, 1)
     result["config"] = {"workload": w.name, "records": n, "prefixes": w.table.n,
                         "n_bins": w.n_bins, "bin_width_ms": w.bin_width, "strategy": strategy,
                         "tune_ms": tune, "l2": f"inputs larger than L2 ({RECORD_BYTES * n / 1e9:.1f} GB of records)",
-                        "policy": "exclusive", "parallelism": f"replicas x{world} (weak)",
+                        "policy": "exclusive", "parallelism": {
+                            "single": "1 GPU", "replicas": f"replicas x{world} (weak)",
+                            "records": f"record-range split x{world} + NCCL reduce-scatter of the "
+                                       "histogram in every step (strong)",
+                            "time": f"owned bin ranges x{world}, no collective (strong)"}[mode],
+                        "records_this_rank": n,
                         "gen_s": round(t_gen, 1), "seed": seed,
                         "data_sha256_prefix": data_digest([h["ts"], h["src"], h["dst"], h["bytes"]])}
     result["clocks"] = clk
@@ -884,12 +987,12 @@ def main():
     # Two buffer sets on two streams: the host link carries one direction at
     # a time per stream, so step k's histogram read-back overlaps step k+1's
     # record upload (the steady state of a stream of days).
-    if not args.no_e2e:
+    if extras and not args.no_e2e:
         nbuf = 2
         dsets = [d] + [{k: torch.empty_like(v) for k, v in d.items()} for _ in range(nbuf - 1)]
-        outs = [out] + [sinet.Histogram(w.n_bins, dev, zero=False) for _ in range(nbuf - 1)]
-        houts = [{"count": torch.empty((2, w.n_bins), dtype=torch.int32, pin_memory=True),
-                  "bytes": torch.empty((2, w.n_bins), dtype=torch.int64, pin_memory=True),
+        outs = [out] + [sinet.Histogram(win.n_bins, dev, zero=False) for _ in range(nbuf - 1)]
+        houts = [{"count": torch.empty((2, win.n_bins), dtype=torch.int32, pin_memory=True),
+                  "bytes": torch.empty((2, win.n_bins), dtype=torch.int64, pin_memory=True),
                   "stats": torch.empty(8, dtype=torch.int64, pin_memory=True)} for _ in range(nbuf)]
         e2e_streams = [torch.cuda.Stream(dev) for _ in range(nbuf)]
 
@@ -927,19 +1030,19 @@ def main():
 
     # post-processing of the day histogram: hourly and ten-minute roll-ups and
     # the sparse form (each reads the 24 B per bin of the dense histogram)
-    if not args.no_post and w.bin_width == 1:
+    if extras and not args.no_post and w.bin_width == 1:
         post = {}
-        hist_bytes = BIN_BYTES * w.n_bins
+        hist_bytes = BIN_BYTES * win.n_bins
         for name, fn in (("rollup_10min", lambda: sinet.rollup(out, 600_000, out=coarse10)),
                          ("rollup_1h", lambda: sinet.rollup(out, 3_600_000, out=coarse1h)),
                          ("sparse", lambda: sinet.sinet_histogram_sparse(
-                             out.c(), w.n_bins, sp_bin, sp_c[0], sp_c[1], sp_b[0], sp_b[1], w.n_bins, sp_n))):
+                             out.c(), win.n_bins, sp_bin, sp_c[0], sp_c[1], sp_b[0], sp_b[1], win.n_bins, sp_n))):
             if name == "rollup_10min":
-                coarse10 = sinet.Histogram(-(-w.n_bins // 600_000), dev, zero=False)
-                coarse1h = sinet.Histogram(-(-w.n_bins // 3_600_000), dev, zero=False)
-                sp_bin = torch.empty(w.n_bins, dtype=torch.int32, device=dev)
-                sp_c = torch.empty((2, w.n_bins), dtype=torch.int32, device=dev)
-                sp_b = torch.empty((2, w.n_bins), dtype=torch.int64, device=dev)
+                coarse10 = sinet.Histogram(-(-win.n_bins // 600_000), dev, zero=False)
+                coarse1h = sinet.Histogram(-(-win.n_bins // 3_600_000), dev, zero=False)
+                sp_bin = torch.empty(win.n_bins, dtype=torch.int32, device=dev)
+                sp_c = torch.empty((2, win.n_bins), dtype=torch.int32, device=dev)
+                sp_b = torch.empty((2, win.n_bins), dtype=torch.int64, device=dev)
                 sp_n = torch.zeros(1, dtype=torch.int64, device=dev)
             fn()
             torch.cuda.synchronize()
@@ -958,7 +1061,7 @@ def main():
         hs = h["src"][: 1 << 20].numpy().view(np.uint32)
         wnet = np.unique(rng.choice(hs, 877)).astype(np.uint32)
         watch = sinet.PrefixTable(wnet, np.full(len(wnet), 32, np.uint8))
-        wp = sinet.HistParams(w.t0, w.bin_width, w.n_bins, watch=watch)
+        wp = sinet.HistParams(win.t0, win.width, win.n_bins, watch=watch)
 
         def watched():
             sinet.discriminate_histogram(table, d["ts"], d["src"], d["dst"], d["bytes"], wp, out)
@@ -979,7 +1082,8 @@ def main():
         # the split entry points: Algorithm 1 alone (class bytes out), then the
         # histogram of those classes (8 + 1 and 12 + 1 bytes per record read)
         cls = torch.empty(n, dtype=torch.uint8, device=dev)
-        hp = sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy="priv_tile", hints=hints)
+        hp = sinet.HistParams(win.t0, win.width, win.n_bins, strategy="priv_tile" if hints else "atomic_cell",
+                              hints=hints)
         for name, fn, per_rec in (
                 ("discriminate", lambda: sinet.discriminate(table, d["src"], d["dst"], cls), 9),
                 ("histogram_from_classes", lambda: sinet.histogram(d["ts"], d["bytes"], cls, hp, out), 13)):
@@ -992,20 +1096,15 @@ def main():
             p1.record(stream)
             torch.cuda.synchronize()
             ms = p0.elapsed_time(p1) / 5
-            extra = BIN_BYTES * w.n_bins if name == "histogram_from_classes" else 0
+            extra = BIN_BYTES * win.n_bins if name == "histogram_from_classes" else 0
             post[name] = {"ms": ms, "sessions_per_s": n / (ms / 1e3),
                           "algorithmic_GBs": (per_rec * n + extra) / (ms / 1e3) / 1e9}
         del cls
         result["post"] = post
         del sp_bin, sp_c, sp_b
 
-    if rank == 0 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(result), flush=True)
     table.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return result
 
 
 if __name__ == "__main__":
