@@ -116,6 +116,11 @@ typedef enum {
 
 /* Input hints (sinet_hist_params.hints). */
 #define SINET_HINT_TIME_SORTED 1u  /* records are (nearly) sorted by ts */
+#define SINET_HINT_TUNE 2u         /* strategy AUTO, not accumulating: the first call of an input class
+                                      (lookup form, sortedness, log2 of n_bins and of n, unit width,
+                                      two-direction policy) times every candidate strategy on its own
+                                      input, synchronising the stream, and the fastest is cached for
+                                      the process; later AUTO calls of the class run it directly */
 
 typedef struct sinet_prefix_table sinet_prefix_table;
 
@@ -325,9 +330,11 @@ typedef struct {
     const uint32_t *bytes;
     uint64_t n;
     const sinet_prefix_table *table;  /* must outlive the batch */
-    sinet_hist_params params;         /* strategy: AUTO, GLOBAL_ATOMIC, ATOMIC_NOAGG or SMEM_FULL;
-                                         lookup: AUTO or INTERVAL; hints, tile_bins and
-                                         block_threads are ignored */
+    sinet_hist_params params;         /* strategy: AUTO, GLOBAL_ATOMIC, ATOMIC_NOAGG, SMEM_FULL or
+                                         SORT_REDUCE (the plain path, run as its own chain of
+                                         kernels after the persistent kernel in the same graph,
+                                         with scratch allocated at creation); lookup: AUTO or
+                                         INTERVAL; hints, tile_bins and block_threads are ignored */
     sinet_hist_out out;               /* device outputs; must outlive the batch */
     const uint32_t *ready;            /* optional device word: when non-NULL the slice's work
                                          items wait until it equals ready_value, so its records
@@ -351,9 +358,11 @@ typedef struct sinet_batch sinet_batch;
  * histogram fits a shared-memory tile, log2 of n_bins and of n, unit bin
  * width, both-direction policy); with SINET_BATCH_AUTOTUNE, each class not
  * yet in the process-wide cache is tuned by timing every candidate strategy
- * on its largest slice (its first 8 M records at most, run as enough copies
- * to keep every CTA busy, into scratch outputs: the slice's own outputs are
- * not touched); the fastest per record is cached and, if the environment
+ * on its largest slice (its first 8 M records at most, into scratch outputs:
+ * the slice's own outputs are not touched). The candidates are the batch
+ * kernel's schemes (warp combining, plain atomics, the whole-histogram tile
+ * when it fits), each run as enough copies to keep every CTA busy, and the
+ * plain path (sort + reduce by key), run as its own chain; the fastest per record is cached and, if the environment
  * variable SINET_AUTOTUNE_CACHE names a file, appended to it as a line
  * "class strategy ns_per_record" (the file is read on first use). Without the flag a class absent from the
  * cache takes a fixed rule. Tuning runs on `stream` and synchronises it.
@@ -404,7 +413,9 @@ sinet_status sinet_batch_destroy(sinet_batch *b);
 typedef struct {
     const sinet_prefix_table *table; /* must outlive the server */
     sinet_hist_params params;        /* window, width, bins, policy; strategy AUTO, GLOBAL_ATOMIC,
-                                        ATOMIC_NOAGG or SMEM_FULL; accumulate is implied */
+                                        ATOMIC_NOAGG or SMEM_FULL (SORT_REDUCE is refused:
+                                        requests share launches of the batch kernel);
+                                        accumulate is implied */
 } sinet_tenant;
 
 typedef struct {
@@ -505,6 +516,18 @@ sinet_status sinet_histogram_rollup(const sinet_hist_out *in, uint64_t n_bins, u
 sinet_status sinet_histogram_sparse(const sinet_hist_out *in, uint64_t n_bins, uint32_t *d_bin, uint32_t *d_count0,
                                     uint32_t *d_count1, uint64_t *d_bytes0, uint64_t *d_bytes1, uint64_t cap,
                                     uint64_t *d_n_out, sinet_stream_t stream);
+
+/*
+ * The strategy (sinet_strategy) that a call of sinet_discriminate_histogram
+ * with these parameters over n records would run: p->strategy unless it is
+ * AUTO; for AUTO, the measured choice cached for the call's input class
+ * (SINET_HINT_TUNE) or else the fixed rule (the whole-histogram tile for
+ * small histograms, the chunk tile for time-sorted input, the 32-byte cells
+ * for unsorted input over a histogram of 256 MB or more, warp combining
+ * otherwise). No kernel runs.
+ */
+sinet_status sinet_auto_strategy(const sinet_prefix_table *t, uint64_t n, const sinet_hist_params *p,
+                                 int32_t *strategy);
 
 /*
  * Read and clear the device status word of the current device, after

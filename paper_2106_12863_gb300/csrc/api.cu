@@ -3,7 +3,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include "api_internal.h"
 #include "owner.h"
@@ -188,6 +190,102 @@ static uint32_t tile_capacity_pair(const DeviceState *ds, uint32_t tsm) {
     return (uint32_t)((per_cta - used) / 16) & ~3u;
 }
 
+// What AUTO runs without a measurement: the whole-histogram tile for small
+// histograms, the chunk tile for time-sorted input, the cells for unsorted
+// input over a histogram far beyond L2, warp combining otherwise.
+static int auto_rule(const sinet_hist_params *p, const RecArgs &r, uint32_t cap) {
+    if (2ull * p->n_bins <= 8192 && p->n_bins <= cap) return SINET_STRAT_SMEM_FULL;
+    // the tile strategy: measured faster than OWNER on the paper-shaped day
+    // (about 4.6 records per ms bin, +-500 ms disorder)
+    if (p->hints & SINET_HINT_TIME_SORTED) return SINET_STRAT_PRIV_TILE;
+    // measured faster than the hot/cold partition on the Zipf-skewed heavy day
+    if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4) return SINET_STRAT_ATOMIC_CELL;
+    return SINET_STRAT_GLOBAL_ATOMIC;
+}
+
+// Strategies a measured AUTO times for a call like this one.
+static int auto_candidates(const sinet_hist_params *p, const RecArgs &r, uint32_t cap, int lk, uint32_t tsm,
+                           const HistArgs &h, const DeviceState *ds, int out[4]) {
+    int k = 0;
+    if (2ull * p->n_bins <= 8192 && p->n_bins <= cap) {
+        out[k++] = SINET_STRAT_SMEM_FULL;
+        out[k++] = SINET_STRAT_GLOBAL_ATOMIC;
+        return k;
+    }
+    if (p->hints & SINET_HINT_TIME_SORTED) {
+        out[k++] = SINET_STRAT_PRIV_TILE;
+        out[k++] = SINET_STRAT_OWNER;
+    }
+    out[k++] = SINET_STRAT_GLOBAL_ATOMIC;
+    if (24 * p->n_bins >= kCellMinHistBytes) out[k++] = SINET_STRAT_ATOMIC_CELL;
+    PartPlan probe{};
+    if (k < 4 && !(p->hints & SINET_HINT_TIME_SORTED) &&
+        plan_partition(lk, tsm, r, h, 0, ds->sm_count, ds->smem_optin, &probe) == cudaSuccess)
+        out[k++] = SINET_STRAT_PARTITION;
+    return k;
+}
+
+// Process-wide cache of measured AUTO choices, by device and input class.
+static std::mutex g_auto_mu;
+static std::map<std::string, int> g_auto;
+
+static std::string auto_key(int dev, int lk, const sinet_hist_params *p, const RecArgs &r, const HistArgs &h) {
+    auto lg = [](uint64_t v) {
+        uint32_t l = 0;
+        while (v > 1) {
+            v >>= 1;
+            ++l;
+        }
+        return l;
+    };
+    char b[128];
+    std::snprintf(b, sizeof b, "d%d/lk%d/sorted%u/bins2^%u/n2^%u/w1%u/two%u", dev, lk,
+                  (p->hints & SINET_HINT_TIME_SORTED) ? 1u : 0u, lg(p->n_bins), lg(r.g.n + 1), h.w_is_one,
+                  h.two_dir);
+    return b;
+}
+
+static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs &r,
+                             const sinet_hist_params *p, const sinet_hist_out *o, cudaStream_t s);
+
+// Measured AUTO: time every candidate once on this call's own input (each
+// overwrites the outputs in full), keep the fastest for the class. The
+// caller then runs the winner, which leaves the outputs right.
+static sinet_status measure_auto(const sinet_prefix_table *t, int lk, const RecArgs &r, const sinet_hist_params *p,
+                                 const sinet_hist_out *o, cudaStream_t s, const int *cands, int nc, int *best) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SINET_CUDA(cudaEventCreate(&e0));
+    SINET_CUDA(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    *best = -1;
+    sinet_status st = SINET_OK;
+    for (int i = 0; i < nc && st == SINET_OK; ++i) {
+        sinet_hist_params pc = *p;
+        pc.strategy = cands[i];
+        pc.hints &= ~SINET_HINT_TUNE;
+        cudaError_t e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) {
+            st = run_hist(t, lk, r, &pc, o, s);
+            if (st == SINET_ERR_UNSUPPORTED) {  // not for this input: not a candidate
+                st = SINET_OK;
+                continue;
+            }
+        }
+        if (e == cudaSuccess && st == SINET_OK) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess && st == SINET_OK) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess && st == SINET_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) st = cuda_fail(e);
+        if (st == SINET_OK && (*best < 0 || ms < best_ms)) {
+            *best = cands[i];
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 // The histogram step for every strategy (records already validated).
 static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs &r,
                              const sinet_hist_params *p, const sinet_hist_out *o, cudaStream_t s) {
@@ -215,22 +313,31 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     // a watch list keeps few records (a blocklist): the plain combining kernel
     if (strat == SINET_STRAT_AUTO && watch) strat = SINET_STRAT_GLOBAL_ATOMIC;
     if (strat == SINET_STRAT_AUTO) {
-        if (2ull * p->n_bins <= 8192 && p->n_bins <= cap)
-            strat = SINET_STRAT_SMEM_FULL;
-        else if (p->hints & SINET_HINT_TIME_SORTED)
-            // the tile strategy: measured faster than OWNER on the paper-shaped
-            // day (about 4.6 records per ms bin, +-500 ms disorder)
-            strat = SINET_STRAT_PRIV_TILE;
-        else if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4) {
-            // unsorted input over a histogram far beyond L2: the hot/cold
-            // partition where its limits allow, else the cells
-            PartPlan probe{};
-            strat = plan_partition(lk, tsm, r, h, 0, ds->sm_count, ds->smem_optin, &probe) == cudaSuccess
-                        ? SINET_STRAT_PARTITION
-                        : SINET_STRAT_ATOMIC_CELL;
+        strat = auto_rule(p, r, cap);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const std::string key = auto_key(dev, lk, p, r, h);
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk_(g_auto_mu);
+            auto it = g_auto.find(key);
+            if (it != g_auto.end()) {
+                strat = it->second;
+                cached = true;
+            }
         }
-        else
-            strat = SINET_STRAT_GLOBAL_ATOMIC;
+        if (!cached && (p->hints & SINET_HINT_TUNE) && !p->accumulate && r.g.n > 0) {
+            int cands[4];
+            const int nc = auto_candidates(p, r, cap, lk, tsm, h, ds, cands);
+            int best = -1;
+            st = measure_auto(t, lk, r, p, o, s, cands, nc, &best);
+            if (st != SINET_OK) return st;
+            if (best >= 0) {
+                strat = best;
+                std::lock_guard<std::mutex> lk_(g_auto_mu);
+                g_auto[key] = best;
+            }
+        }
     }
 
     // launch shapes first, so an unsupported combination fails before anything is enqueued
@@ -590,6 +697,37 @@ sinet_status sinet_discriminate_histogram(const sinet_prefix_table *t, const uin
     r.bytes = d_bytes;
     r.g = make_geom(n, {{d_ts, 8}, {d_src, 4}, {d_dst, 4}, {d_bytes, 4}});
     return run_hist(t, lk, r, p, o, stream);
+}
+
+sinet_status sinet_auto_strategy(const sinet_prefix_table *t, uint64_t n, const sinet_hist_params *p,
+                                 int32_t *strategy) {
+    if (!t || !strategy) return SINET_ERR_INVALID_ARG;
+    sinet_status st = check_params(p);
+    if (st != SINET_OK) return st;
+    if (n > kMaxN) return SINET_ERR_INVALID_ARG;
+    const int lk = pick_lookup(t, p->lookup, &st);
+    if (st != SINET_OK) return st;
+    DeviceState *ds = nullptr;
+    if ((st = device_state(&ds)) != SINET_OK) return st;
+    if (p->strategy != SINET_STRAT_AUTO) {
+        *strategy = p->strategy;
+        return SINET_OK;
+    }
+    if (p->watch) {
+        *strategy = SINET_STRAT_GLOBAL_ATOMIC;
+        return SINET_OK;
+    }
+    RecArgs r{};
+    r.g.n = n;
+    sinet_hist_out o{};
+    HistArgs h = make_hist(p, &o);
+    *strategy = auto_rule(p, r, tile_capacity(ds, table_smem(t, lk)));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk_(g_auto_mu);
+    auto it = g_auto.find(auto_key(dev, lk, p, r, h));
+    if (it != g_auto.end()) *strategy = it->second;
+    return SINET_OK;
 }
 
 sinet_status sinet_device_status(sinet_stream_t stream, uint32_t *device_code) {

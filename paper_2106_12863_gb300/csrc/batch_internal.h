@@ -22,7 +22,7 @@ constexpr uint32_t kTuneCopies = 64;
 
 struct PlannedSlice {
     BatchSlice d;
-    uint32_t items = 0;       // work items
+    uint32_t items = 0;       // work items (0 for a slice run by the plain path)
     uint32_t zero_items = 0;  // zeroing items (0 when accumulating)
     int32_t strategy = 0;     // sinet_strategy; AUTO until resolved
     bool tile_fits = false;   // the whole histogram fits a tile next to the table
@@ -49,12 +49,27 @@ sinet_status resolve_strategies(std::vector<PlannedSlice> &v, bool tune, const D
 // Map a public strategy to the batch kernel's update scheme.
 uint32_t batch_scheme(int32_t strategy);
 
+// A slice run by the plain path (discriminate, radix sort, reduce by key) as
+// its own chain of kernels in the batch's graph, after the persistent kernel.
+struct SortJob {
+    RecArgs r;
+    TableArgs t;
+    HistArgs h;
+    int lk = 0;
+    SortPlan plan{};
+    void *scratch = nullptr;  // plan.scratch_bytes, owned by the engine
+};
+
+// Whether the plain path can run a slice (its emitted pairs are counted in 32 bits).
+bool sort_feasible(const PlannedSlice &ps);
+
 // Device-resident descriptors + the captured launch.
 struct BatchEngine {
     int device = 0;
     uint32_t cap = 0;  // slices
     uint32_t smem = 0;
     int grid = 0, zgrid = 0;
+    int sm_count = 0;
     void *d_mem = nullptr;
     size_t bytes = 0;
     size_t off_item = 0, off_zero = 0, off_slices = 0;
@@ -62,11 +77,14 @@ struct BatchEngine {
     uint64_t wait_ns = 2000000000ull;  // bound of a ready-word wait
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<SortJob> sorts;  // slices run by the plain path, after the batch kernel
 
     sinet_status init(uint32_t capacity, const DeviceState *ds, uint32_t smem_bytes);
     // host image (header, starts, descriptors) of `v` in descriptor order
     void image(const std::vector<PlannedSlice> &v, std::vector<uint8_t> &buf) const;
-    sinet_status capture(uint32_t *status);  // capture zero + batch kernels as a graph
+    // scratch for the slices of v run by the plain path (before capture)
+    sinet_status plan_sorts(const std::vector<PlannedSlice> &v, const DeviceState *ds);
+    sinet_status capture(uint32_t *status);  // capture zero + batch kernels (+ plain chains) as a graph
     sinet_status launch(cudaStream_t s) const;
     void release();
 };

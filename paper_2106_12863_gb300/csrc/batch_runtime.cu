@@ -27,9 +27,14 @@ uint32_t batch_grid(const DeviceState *ds) { return 2u * (uint32_t)ds->sm_count;
 uint32_t batch_scheme(int32_t strategy) {
     switch (strategy) {
         case SINET_STRAT_SMEM_FULL: return BS_TILE;
-        case SINET_STRAT_ATOMIC_NOAGG: return BS_NOAGG;
+        case SINET_STRAT_ATOMIC_NOAGG:
+        case SINET_STRAT_SORT_REDUCE: return BS_NOAGG;  // the plain path takes no work items
         default: return BS_AGG;
     }
+}
+
+bool sort_feasible(const PlannedSlice &ps) {
+    return ps.d.r.g.n * (ps.d.h.two_dir ? 2ull : 1ull) < 0xFFFFFFF0ull;
 }
 
 static uint32_t round16(uint32_t v) { return (v + 15u) & ~15u; }
@@ -44,7 +49,9 @@ void set_strategy(PlannedSlice &ps, int32_t strategy, uint32_t grid) {
     ps.strategy = strategy;
     ps.d.strat = batch_scheme(strategy);
     ps.d.item_quads = item_quads_for(ps.d.r.g.quads, ps.d.strat, grid);
-    ps.items = (uint32_t)((ps.d.r.g.quads + ps.d.item_quads - 1) / ps.d.item_quads);
+    ps.items = strategy == SINET_STRAT_SORT_REDUCE
+                   ? 0u
+                   : (uint32_t)((ps.d.r.g.quads + ps.d.item_quads - 1) / ps.d.item_quads);
 }
 
 sinet_status check_slice(const sinet_batch_slice &u) {
@@ -58,7 +65,7 @@ sinet_status check_slice(const sinet_batch_slice &u) {
         return SINET_ERR_INVALID_ARG;
     const int32_t s = u.params.strategy;
     if (s != SINET_STRAT_AUTO && s != SINET_STRAT_GLOBAL_ATOMIC && s != SINET_STRAT_ATOMIC_NOAGG &&
-        s != SINET_STRAT_SMEM_FULL)
+        s != SINET_STRAT_SMEM_FULL && s != SINET_STRAT_SORT_REDUCE)
         return SINET_ERR_UNSUPPORTED;
     if (u.params.lookup == SINET_LOOKUP_PML || u.params.watch) return SINET_ERR_UNSUPPORTED;
     return SINET_OK;
@@ -91,6 +98,7 @@ sinet_status plan_slice(const sinet_batch_slice &u, const DeviceState *ds, uint3
     d.ready = u.ready;
     d.ready_value = u.ready_value;
     if (u.params.strategy == SINET_STRAT_SMEM_FULL && !ps.tile_fits) return SINET_ERR_UNSUPPORTED;
+    if (u.params.strategy == SINET_STRAT_SORT_REDUCE && !sort_feasible(ps)) return SINET_ERR_UNSUPPORTED;
     set_strategy(ps, u.params.strategy, batch_grid(ds));  // AUTO: resolved later
     ps.zero_items = d.zero ? (uint32_t)((u.params.n_bins + kZeroBins - 1) / kZeroBins) : 0u;
     return SINET_OK;
@@ -108,6 +116,7 @@ sinet_status BatchEngine::init(uint32_t capacity, const DeviceState *ds, uint32_
     if (per_sm < 1) return SINET_ERR_UNSUPPORTED;
     grid = per_sm * ds->sm_count;
     zgrid = 4 * ds->sm_count;
+    sm_count = ds->sm_count;
     off_item = sizeof(BatchHeader);
     off_zero = off_item + 4 * ((size_t)cap + 1);
     off_slices = (off_zero + 4 * ((size_t)cap + 1) + 15) & ~(size_t)15;
@@ -145,6 +154,22 @@ void BatchEngine::image(const std::vector<PlannedSlice> &v, std::vector<uint8_t>
     std::memcpy(buf.data(), &hdr, sizeof hdr);
 }
 
+sinet_status BatchEngine::plan_sorts(const std::vector<PlannedSlice> &v, const DeviceState *ds) {
+    (void)ds;
+    for (const PlannedSlice &ps : v) {
+        if (ps.strategy != SINET_STRAT_SORT_REDUCE) continue;
+        SortJob j;
+        j.r = ps.d.r;
+        j.t = ps.d.t;
+        j.h = ps.d.h;
+        j.lk = (int)ps.d.lk;
+        j.plan = plan_sort_reduce(ps.d.r.g.n, ps.d.h.n_bins, ps.d.h.two_dir != 0);
+        SINET_CUDA(cudaMalloc(&j.scratch, std::max<size_t>(j.plan.scratch_bytes, 256)));
+        sorts.push_back(j);
+    }
+    return SINET_OK;
+}
+
 sinet_status BatchEngine::capture(uint32_t *status) {
     cudaStream_t cs = nullptr;
     SINET_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -152,6 +177,16 @@ sinet_status BatchEngine::capture(uint32_t *status) {
     if (e == cudaSuccess) {
         cudaError_t e1 = run_batch_zero(args, zgrid, cs);
         cudaError_t e2 = e1 == cudaSuccess ? run_batch(args, smem, grid, cs, status) : e1;
+        // slices on the plain path: their outputs were zeroed (or are
+        // accumulated into) like every other slice's, so the chain adds
+        LaunchCfg lc;
+        lc.stream = cs;
+        lc.status = status;
+        for (const SortJob &j : sorts) {
+            if (e2 != cudaSuccess) break;
+            lc.sm_count = sm_count;
+            e2 = run_sort_reduce(j.lk, j.r, j.t, j.h, j.plan, j.scratch, true, lc);
+        }
         e = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
     }
@@ -169,6 +204,9 @@ void BatchEngine::release() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (d_mem) cudaFree(d_mem);
+    for (SortJob &j : sorts)
+        if (j.scratch) cudaFree(j.scratch);
+    sorts.clear();
     exec = nullptr;
     graph = nullptr;
     d_mem = nullptr;
@@ -189,6 +227,7 @@ const char *strategy_name(int32_t s) {
         case SINET_STRAT_GLOBAL_ATOMIC: return "global_atomic";
         case SINET_STRAT_ATOMIC_NOAGG: return "atomic_noagg";
         case SINET_STRAT_SMEM_FULL: return "smem_full";
+        case SINET_STRAT_SORT_REDUCE: return "sort_reduce";
     }
     return "auto";
 }
@@ -197,6 +236,7 @@ int32_t strategy_from_name(const char *s) {
     if (!std::strcmp(s, "global_atomic")) return SINET_STRAT_GLOBAL_ATOMIC;
     if (!std::strcmp(s, "atomic_noagg")) return SINET_STRAT_ATOMIC_NOAGG;
     if (!std::strcmp(s, "smem_full")) return SINET_STRAT_SMEM_FULL;
+    if (!std::strcmp(s, "sort_reduce")) return SINET_STRAT_SORT_REDUCE;
     return -1;
 }
 
@@ -329,6 +369,50 @@ sinet_status tune_one(const PlannedSlice &rep, const DeviceState *ds, uint32_t s
             *best_ns = ns;
         }
     }
+    // the plain path: its own chain of kernels over the slice's first n
+    // records into scratch outputs, timed the same way (best of three after a
+    // warm-up run)
+    if (st == SINET_OK && sort_feasible(ps)) {
+        const SortPlan plan = plan_sort_reduce(n, nb, ps.d.h.two_dir != 0);
+        void *scratch = nullptr, *outs = nullptr;
+        cudaError_t e = cudaMalloc(&scratch, std::max<size_t>(plan.scratch_bytes, 256));
+        if (e == cudaSuccess) e = cudaMalloc(&outs, out_bytes);
+        HistArgs h = ps.d.h;
+        if (e == cudaSuccess) {
+            uint8_t *m = static_cast<uint8_t *>(outs);
+            h.cnt[0] = reinterpret_cast<uint32_t *>(m);
+            h.cnt[1] = h.cnt[0] + nb;
+            h.byt[0] = reinterpret_cast<uint64_t *>(m + (((size_t)8 * nb + 15) & ~(size_t)15));
+            h.byt[1] = h.byt[0] + nb;
+            h.stats = h.byt[1] + nb;
+        }
+        LaunchCfg lc;
+        lc.stream = s;
+        lc.status = ds->status;
+        lc.sm_count = ds->sm_count;
+        float ms = 1e30f;
+        for (int rep_i = 0; rep_i < 4 && e == cudaSuccess; ++rep_i) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(outs, 0, out_bytes, s);
+            if (e == cudaSuccess) e = run_sort_reduce((int)ps.d.lk, ps.d.r, ps.d.t, h, plan, scratch, true, lc);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && rep_i > 0) ms = std::min(ms, t);
+        }
+        if (scratch) cudaFree(scratch);
+        if (outs) cudaFree(outs);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e);
+        } else {
+            const float ns = ms * 1e6f / (float)std::max<uint64_t>(n, 1);
+            if (*best < 0 || ns < *best_ns) {
+                *best = SINET_STRAT_SORT_REDUCE;
+                *best_ns = ns;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
@@ -375,6 +459,7 @@ sinet_status resolve_strategies(std::vector<PlannedSlice> &v, bool tune, const D
         auto it = g_tune.find(keys[i]);
         int32_t s_ = it != g_tune.end() ? it->second : fixed_rule(v[i]);
         if (s_ == SINET_STRAT_SMEM_FULL && !v[i].tile_fits) s_ = fixed_rule(v[i]);
+        if (s_ == SINET_STRAT_SORT_REDUCE && !sort_feasible(v[i])) s_ = fixed_rule(v[i]);
         set_strategy(v[i], s_, batch_grid(ds));
     }
     return SINET_OK;
@@ -433,6 +518,7 @@ sinet_status sinet_batch_create(const sinet_batch_slice *slices, uint32_t n_slic
     b->items = items;
     b->records = records;
     st = b->eng.init(n_slices, ds, smem);
+    if (st == SINET_OK) st = b->eng.plan_sorts(v, ds);
     std::vector<uint8_t> buf;
     if (st == SINET_OK) {
         b->eng.image(v, buf);

@@ -431,20 +431,32 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
                 break;
             }
             const uint8_t *sp = stage + s * kPartStageBytes;
-            const ulonglong2 ts2 = *reinterpret_cast<const ulonglong2 *>(sp + 16 * tid);
-            const uint2 s2 = *reinterpret_cast<const uint2 *>(sp + 8 * R + 8 * tid);
-            const uint2 d2 = *reinterpret_cast<const uint2 *>(sp + 12 * R + 8 * tid);
-            const uint2 b2 = *reinterpret_cast<const uint2 *>(sp + 16 * R + 8 * tid);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
-            uint32_t a[2] = {s2.x, s2.y}, in_s[2], in_d[2];
-            C.template in_n<2>(a, in_s);
-            a[0] = d2.x;
-            a[1] = d2.y;
-            C.template in_n<2>(a, in_d);
-            part_record<W1>(h, p, m, ts2.x, b2.x, in_s[0] | in_d[0] << 1, ccp, oorp, status);
-            part_record<W1>(h, p, m, ts2.y, b2.y, in_s[1] | in_d[1] << 1, ccp, oorp, status);
-            // two records per thread per stage: drain well before a 16-bit field fills
+            if (kPartRPT == 2) {
+                const ulonglong2 ts2 = *reinterpret_cast<const ulonglong2 *>(sp + 16 * tid);
+                const uint2 s2 = *reinterpret_cast<const uint2 *>(sp + 8 * R + 8 * tid);
+                const uint2 d2 = *reinterpret_cast<const uint2 *>(sp + 12 * R + 8 * tid);
+                const uint2 b2 = *reinterpret_cast<const uint2 *>(sp + 16 * R + 8 * tid);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
+                uint32_t a[2] = {s2.x, s2.y}, in_s[2], in_d[2];
+                C.template in_n<2>(a, in_s);
+                a[0] = d2.x;
+                a[1] = d2.y;
+                C.template in_n<2>(a, in_d);
+                part_record<W1>(h, p, m, ts2.x, b2.x, in_s[0] | in_d[0] << 1, ccp, oorp, status);
+                part_record<W1>(h, p, m, ts2.y, b2.y, in_s[1] | in_d[1] << 1, ccp, oorp, status);
+            } else {
+                const uint64_t ts1 = *reinterpret_cast<const uint64_t *>(sp + 8 * tid);
+                const uint32_t s1 = *reinterpret_cast<const uint32_t *>(sp + 8 * R + 4 * tid);
+                const uint32_t d1 = *reinterpret_cast<const uint32_t *>(sp + 12 * R + 4 * tid);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(sp + 16 * R + 4 * tid);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
+                uint32_t a[2] = {s1, d1}, in_a[2];
+                C.template in_n<2>(a, in_a);
+                part_record<W1>(h, p, m, ts1, b1, in_a[0] | in_a[1] << 1, ccp, oorp, status);
+            }
+            // at most two records per thread per stage: drain well before a 16-bit field fills
             if (++since == 16384) {
                 drain_packed(ccp, oorp, s_cnt);
                 since = 0;
@@ -543,7 +555,7 @@ __global__ void __launch_bounds__(256) k_part_list_pages(PartDev p) {
 
 namespace {
 
-constexpr uint32_t kRunChunk = 2048;  // pages whose runs one staging of the run table covers
+constexpr uint32_t kRunChunk = 1024;  // pages whose runs one staging of the run table covers
 
 struct ColdSmem {
     uint64_t *buf[2];  // [kPartPage] pages as loaded (two, for the copy of the next)

@@ -27,6 +27,8 @@ namespace sinet {
 constexpr int kPartConsumers = 512;                 // consumer threads of the main pass
 constexpr int kPartThreads = kPartConsumers + 32;   // plus one producer warp (TMA)
 constexpr uint32_t kPartStageRecords = 1024;        // records per TMA stage
+constexpr int kPartRPT = kPartStageRecords / kPartConsumers;  // records per consumer per stage (1 or 2)
+static_assert(kPartRPT == 1 || kPartRPT == 2, "one or two records per consumer thread and stage");
 constexpr uint32_t kPartStages = 4;
 constexpr uint32_t kPartStageBytes = 20 * kPartStageRecords;
 constexpr uint32_t kPartPageBits = 11;              // 2,048 entries (16 KB) per page

@@ -315,6 +315,9 @@ sinet_status sinet_server_create(const sinet_server_config *cfg, const sinet_ten
         u.out.stats = reinterpret_cast<uint64_t *>(16);
         const sinet_status st = check_slice(u);
         if (st != SINET_OK) return st;
+        // requests join shared launches of the batch kernel: the plain path,
+        // a chain of its own per slice, is not run by the server
+        if (u.params.strategy == SINET_STRAT_SORT_REDUCE) return SINET_ERR_UNSUPPORTED;
     }
     DeviceState *ds = nullptr;
     sinet_status st = device_state(&ds);

@@ -33,6 +33,7 @@ STRATEGIES = {"auto": STRAT_AUTO, "global_atomic": STRAT_GLOBAL_ATOMIC,
 LOOKUP_AUTO, LOOKUP_INTERVAL, LOOKUP_PML = range(3)
 LOOKUPS = {"auto": LOOKUP_AUTO, "interval": LOOKUP_INTERVAL, "pml": LOOKUP_PML}
 HINT_TIME_SORTED = 1
+HINT_TUNE = 2
 
 DIR_OUT, DIR_IN = 1, 2
 EXCLUSIVE = (0, DIR_OUT, DIR_IN, 0)
@@ -122,6 +123,7 @@ def load():
                                                                 ctypes.POINTER(HistParamsC),
                                                                 ctypes.POINTER(HistOutC), _P]),
         "sinet_device_status": (ctypes.c_int, [_P, _P]),
+        "sinet_auto_strategy": (ctypes.c_int, [_P, u64, ctypes.POINTER(HistParamsC), _P]),
         "sinet_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchSliceC), u32, u32, _P, _P]),
         "sinet_batch_run": (ctypes.c_int, [_P, _P]),
         "sinet_batch_strategy": (ctypes.c_int, [_P, u32, _P]),
@@ -429,6 +431,14 @@ def discriminate(table: PrefixTable, src, dst, cls=None, lookup="auto", stream=N
 def histogram(ts, nbytes, cls, params: HistParams, out: Histogram, stream=None):
     sinet_histogram(ts, nbytes, cls, ts.numel(), params.c(), out.c(), stream)
     return out
+
+
+def auto_strategy(table: "PrefixTable", n: int, params: "HistParams") -> str:
+    """The strategy AUTO would run for n records with these parameters."""
+    v = ctypes.c_int32()
+    _check(load().sinet_auto_strategy(table.handle, n, ctypes.byref(params.c()), ctypes.byref(v)),
+           "sinet_auto_strategy")
+    return next(k for k, x in STRATEGIES.items() if x == v.value)
 
 
 def bin_index(ts, t0_ms: int, bin_width_ms: int, n_bins: int, out=None, stream=None):

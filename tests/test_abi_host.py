@@ -231,7 +231,8 @@ def test_batch_validation_rejects_before_any_cuda_call():
     c = good(); c.params.bin_width_ms = 0; bad.append((c, 1))
     c = good(); c.ts = 0x40004; bad.append((c, 1))
     c = good(); c.out.stats = None; bad.append((c, 1))
-    c = good(); c.params.strategy = sinet.STRAT_SORT_REDUCE; bad.append((c, 8))
+    c = good(); c.params.strategy = sinet.STRAT_OWNER; bad.append((c, 8))
+    c = good(); c.params.strategy = sinet.STRAT_PARTITION; bad.append((c, 8))
     c = good(); c.params.strategy = sinet.STRAT_PRIV_TILE; bad.append((c, 8))
     c = good(); c.params.lookup = sinet.LOOKUP_PML; bad.append((c, 8))
     for c, want in bad:
@@ -257,6 +258,8 @@ def test_server_validation_rejects_before_any_cuda_call():
     bad[0].table = 0x1000
     bad[0].params = sinet.HistParams(0, 0, 10).c()  # zero bin width
     assert L.sinet_server_create(ctypes.byref(good), bad, 1, ctypes.byref(h)) == 1
+    bad[0].params = sinet.HistParams(0, 1, 10, strategy="sort_reduce").c()  # not run by the server
+    assert L.sinet_server_create(ctypes.byref(good), bad, 1, ctypes.byref(h)) == 8
     t = ctypes.c_uint64()
     assert L.sinet_server_submit(None, 0, None, None, None, None, 0, ctypes.byref(t)) == 1
     assert L.sinet_server_wait(None, 1, 0, None) == 1
@@ -410,7 +413,8 @@ def test_ctypes_layouts_and_constants_match_the_header(tmp_path):
     consts = {f"SINET_STRAT_{k.upper()}": v for k, v in sinet.STRATEGIES.items()}
     consts.update({f"SINET_LOOKUP_{k.upper()}": v for k, v in sinet.LOOKUPS.items()})
     consts.update({name: code for code, name in sinet.STATUS.items()})
-    consts.update({"SINET_HINT_TIME_SORTED": sinet.HINT_TIME_SORTED, "SINET_BATCH_AUTOTUNE": sinet.BATCH_AUTOTUNE,
+    consts.update({"SINET_HINT_TIME_SORTED": sinet.HINT_TIME_SORTED, "SINET_HINT_TUNE": sinet.HINT_TUNE,
+                   "SINET_BATCH_AUTOTUNE": sinet.BATCH_AUTOTUNE,
                    "SINET_DIR_OUT": sinet.DIR_OUT, "SINET_DIR_IN": sinet.DIR_IN})
     # every enum member and flag the header defines has a binding constant
     import re

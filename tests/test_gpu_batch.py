@@ -109,6 +109,10 @@ def _edge_cases():
     # accumulating into an existing histogram, tile scheme and atomics
     cases.append(Case(net, ln, u, 0, 2000, 1800, strategy="smem_full", accumulate=True))
     cases.append(Case(net, ln, u, 0, 1, 3_600_000, strategy="global_atomic", accumulate=True))
+    # the plain path as a chain of its own in the batch's graph: zeroed, and
+    # accumulating, with the inclusive policy (two directions per record)
+    cases.append(Case(net, ln, r, 0, 1, 3_600_000, policy=sinet.INCLUSIVE, strategy="sort_reduce"))
+    cases.append(Case(net, ln, u, 0, 10, 360_000, strategy="sort_reduce", accumulate=True))
     return cases
 
 
@@ -118,14 +122,14 @@ def _check(orc, cases, runs=1):
 
 
 def test_batch_parity_and_replay(orc):
-    cases = _generated(32, 0.01, ["auto", "global_atomic", "atomic_noagg", "smem_full"]) + _edge_cases()
+    cases = _generated(32, 0.01, ["auto", "global_atomic", "atomic_noagg", "smem_full", "sort_reduce"]) + _edge_cases()
     b = sinet.Batch([c.slice() for c in cases])
     items, records = b.info()
     assert records == sum(len(c.rec["ts"]) for c in cases)
     assert items >= len(cases) - 1
     for i, c in enumerate(cases):
         s = b.strategy(i)
-        assert s in ("global_atomic", "atomic_noagg", "smem_full")
+        assert s in ("global_atomic", "atomic_noagg", "smem_full", "sort_reduce")
         if c.params.strategy != "auto":
             assert s == c.params.strategy
     b.run()
@@ -161,7 +165,7 @@ def test_batch_autotune_and_cache(orc, tmp_path, monkeypatch):
     lines = path.read_text().splitlines() if path.exists() else []
     for ln_ in lines:
         key, name, ms = ln_.split()
-        assert key.startswith("sm") and name in ("global_atomic", "atomic_noagg", "smem_full")
+        assert key.startswith("sm") and name in ("global_atomic", "atomic_noagg", "smem_full", "sort_reduce")
         assert float(ms) > 0
     b.run()
     torch.cuda.synchronize()

@@ -323,3 +323,29 @@ def test_watch_filter_refused_where_not_run(orc):
             sinet.discriminate_histogram(t, d["ts"], d["src"], d["dst"], d["bytes"],
                                          sinet.HistParams(w.t0, w.bin_width, w.n_bins, strategy=s, watch=wt), out)
         assert e.value.status == 8
+
+
+# ---------------------------------------------------------------------------
+# AUTO: the fixed rule, and the measured choice (SINET_HINT_TUNE)
+
+
+@pytest.mark.parametrize("key,hints", [("heavy", 0), ("day", sinet.HINT_TIME_SORTED), ("tiny", 0)])
+def test_auto_measured_choice(orc, key, hints):
+    w, net, ln, rec = _workload(key, 600_007)
+    ref = orc.discriminate_histogram(net, ln, rec, w.t0, w.bin_width, w.n_bins)
+    t = sinet.PrefixTable(net, ln)
+    d = to_dev(rec)
+    n = len(rec["ts"])
+    p = sinet.HistParams(w.t0, w.bin_width, w.n_bins, hints=hints)
+    rule = sinet.auto_strategy(t, n, p)
+    assert rule != "auto"
+    got = run_fused(t, d, p)
+    assert_hist_equal(got, ref, f"auto rule {rule}")
+    p.hints = hints | sinet.HINT_TUNE
+    first = run_fused(t, d, p)  # times the candidates, then runs the fastest
+    assert_hist_equal(first, ref, "auto measured (first call)")
+    chosen = sinet.auto_strategy(t, n, p)
+    assert chosen in ("smem_full", "priv_tile", "owner", "global_atomic", "atomic_cell", "partition")
+    assert sinet.auto_strategy(t, n, sinet.HistParams(w.t0, w.bin_width, w.n_bins, hints=hints)) == chosen
+    again = run_fused(t, d, p)  # cached: no timing
+    assert_hist_equal(again, ref, f"auto measured (cached {chosen})")
