@@ -610,6 +610,58 @@ def run_reference_batch(args, o):
     print(json.dumps(line), flush=True)
 
 
+def serve_oracle_check(server, specs, pools, phase, args, tenant=None, k_random=2000, k_hot=200):
+    """Compare a tenant's resident histogram with the oracle.
+
+    Every request of a tenant covered the first n records of the tenant's
+    pool, so record i was added as many times as there were requests longer
+    than i: the expected histogram is, over the segments between consecutive
+    request lengths, the segment's histogram times the number of requests
+    that covered it (counts modulo 2^32, byte sums modulo 2^64). The oracle
+    computes each segment on a sample of bins: random bins, the day's edges
+    and the resident histogram's hottest bins."""
+    import oracle
+
+    o_ = oracle.get()
+    done = phase[0][:max(3, args.warmup)] + phase[0] + phase[1] + phase[2]
+    if tenant is None:  # the tenant with the most records submitted
+        tot = {}
+        for r in done:
+            tot[r.tenant] = tot.get(r.tenant, 0) + r.n
+        tenant = max(tot, key=tot.get)
+    lens = sorted(r.n for r in done if r.tenant == tenant)
+    got = server.export(tenant)
+    nb = got["count"].shape[1]
+    rng = np.random.default_rng(tenant)
+    hot = np.argsort(got["count"][0].astype(np.uint64) + got["count"][1])[::-1][:k_hot]
+    keep = np.unique(np.concatenate([rng.integers(0, nb, k_random), hot, [0, nb - 1]])).astype(np.uint64)
+    net, ln = gen.make_table(specs[tenant], gen.BASE_SEED + 5000 + tenant)
+    pool = pools[tenant]
+    rec = {"ts": pool["ts"].numpy().view(np.uint64), "src": pool["src"].numpy().view(np.uint32),
+           "dst": pool["dst"].numpy().view(np.uint32), "bytes": pool["bytes"].numpy().view(np.uint32)}
+    want_c = np.zeros((2, len(keep)), np.uint64)
+    want_b = np.zeros((2, len(keep)), np.uint64)
+    t0 = time.perf_counter()
+    lo = 0
+    for j, hi in enumerate(lens):
+        if hi > lo:
+            seg = {k: v[lo:hi] for k, v in rec.items()}
+            c, b = o_.histogram_bins(net, ln, seg, 0, 1, nb, keep)
+            mult = np.uint64(len(lens) - j)
+            with np.errstate(over="ignore"):
+                want_c += c.astype(np.uint64) * mult
+                want_b += b * mult
+        lo = hi
+    idx = keep.astype(np.int64)
+    ok_c = np.array_equal((want_c & np.uint64(0xFFFFFFFF)).astype(np.uint32), got["count"][:, idx])
+    ok_b = np.array_equal(want_b, got["bytes"][:, idx])
+    ok_n = int(got["stats"][:4].sum()) == sum(lens)
+    assert ok_c and ok_b and ok_n, f"serving tenant {tenant} differs from the oracle"
+    return {"tenant": tenant, "requests": len(lens), "records_submitted": int(sum(lens)),
+            "bins_compared": int(len(keep)), "hottest_compared": int(k_hot), "bit_exact": True,
+            "oracle_s": round(time.perf_counter() - t0, 1)}
+
+
 def run_serve_bench(args):
     """The serving loop: tenants with resident day histograms; request sizes
     log-normal (median 1 M records, p99 50 M before the cap), each uniform over
@@ -704,6 +756,9 @@ def run_serve_bench(args):
                                  "requests": len(ph), "launches": st["launches"],
                                  "p50_ms": st["p50_latency_ns"] / 1e6, "p99_ms": st["p99_latency_ns"] / 1e6,
                                  "max_ms": st["max_latency_ns"] / 1e6}
+    # full-scale parity: one tenant's resident day histogram, after every
+    # phase, against the oracle over that tenant's requests (sampled bins)
+    serving["oracle_check"] = serve_oracle_check(server, specs, pools, phase, args)
     h2d = RECORD_BYTES * mean_n
     result = {"metric": METRIC, "value": world * sat, "unit": UNIT, "n_gpus": world,
               "steps": len(phase[0]), "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_sat / len(phase[0]),

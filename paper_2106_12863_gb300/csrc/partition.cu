@@ -555,22 +555,50 @@ __global__ void __launch_bounds__(256) k_part_list_pages(PartDev p) {
 
 namespace {
 
-constexpr uint32_t kRunChunk = 1024;  // pages whose runs one staging of the run table covers
+constexpr uint32_t kRunChunk = 1024;      // pages whose runs one staging of the run table covers
+constexpr uint32_t kGroupThreads = 512;   // threads of one page-sorting group
 
-struct ColdSmem {
-    uint64_t *buf[2];  // [kPartPage] pages as loaded (two, for the copy of the next)
-    uint64_t *srt;     // [kPartPage] a page sorted by owner
-    uint32_t *ocnt;    // [g_cold + 1] entries per owner, then their offsets
-    uint32_t *rpid;    // [kRunChunk] run table: page id,
-    uint32_t *rbeg;    //   first entry of this owner's run in the page,
-    uint32_t *rpre;    //   [kRunChunk + 1] prefix of the runs' lengths
-    uint32_t *tile;    // [6][own_bins]: counts d0, d1; byte sums low d0, d1; high d0, d1
+// One page-sorting group's shared state: two page buffers (a copy of the next
+// page lands while this one is sorted), the sorted page, owner counts.
+struct GroupSmem {
+    uint64_t *buf[2];  // [kPartPage]
+    uint64_t *srt;     // [kPartPage]
+    uint32_t *ocnt;    // [g_cold + 1]
     uint64_t *bar;     // [2] page copies
     uint32_t *s_id;    // [2] page id of the copy in flight into buf[k]
     uint32_t *s_fill;  // [2] its entries
+    uint32_t *s_warp;  // [16] scan partials
+    uint32_t *s_flag;  // a wait that ran out
+    uint32_t g;        // group index (named barrier 1 + g)
 };
 
-// Block-wide exclusive scan of v (one value per thread); the total in *total.
+__device__ __forceinline__ void group_sync(uint32_t g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+
+// Group-wide exclusive scan of v (one value per thread of the group).
+__device__ __forceinline__ uint32_t group_scan(uint32_t v, const GroupSmem &gs, uint32_t *total) {
+    const uint32_t t = threadIdx.x % kGroupThreads;
+    const uint32_t lane = t & 31, warp = t >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    group_sync(gs.g);
+    if (lane == 31) gs.s_warp[warp] = incl;
+    group_sync(gs.g);
+    uint32_t woff = 0, tot = 0;
+    for (uint32_t w = 0; w < kGroupThreads / 32; ++w) {
+        if (w < warp) woff += gs.s_warp[w];
+        tot += gs.s_warp[w];
+    }
+    *total = tot;
+    return woff + incl - v;
+}
+
+// Block-wide exclusive scan of v (one value per thread of the whole CTA).
 __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint32_t incl = v;
@@ -591,117 +619,118 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *s_warp, uin
     return woff + incl - v;
 }
 
-// Exclusive scan of ocnt[0 .. n) in place (n <= 4 * blockDim.x), total in ocnt[n].
-__device__ void scan_owners(uint32_t *ocnt, uint32_t n, uint32_t *s_warp) {
-    const uint32_t i0 = 4 * threadIdx.x;
-    uint32_t v[4], sum = 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        v[u] = i0 + u < n ? ocnt[i0 + u] : 0u;
-        sum += v[u];
-    }
-    uint32_t total;
-    uint32_t ex = block_scan(sum, s_warp, &total);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        if (i0 + u < n) ocnt[i0 + u] = ex;
-        ex += v[u];
-    }
-    if (threadIdx.x == 0) ocnt[n] = total;
-}
-
-// Thread 0: start the TMA copy of the page at list position j into buf[k].
-__device__ __forceinline__ void issue_page(const PartDev &p, const ColdSmem &s, uint32_t j, uint32_t k) {
+// The group's thread 0: start the TMA copy of the page at list position j into buf[k].
+__device__ __forceinline__ void issue_page(const PartDev &p, const GroupSmem &gs, uint32_t j, uint32_t k) {
     const uint32_t id = p.page_list[j];
     const uint32_t fill = p.page_fill[id];
-    s.s_id[k] = id;
-    s.s_fill[k] = fill;
+    gs.s_id[k] = id;
+    gs.s_fill[k] = fill;
     const uint32_t bytes = (fill * 8u + 15u) & ~15u;  // within the 16 KB page
-    const uint32_t bar = smem_u32(s.bar + k);
+    const uint32_t bar = smem_u32(gs.bar + k);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of buf[k] first
     mbar_expect_tx(bar, bytes);
-    if (bytes) bulk_g2s(smem_u32(s.buf[k]), p.pages + (uint64_t)id * kPartPage, bytes, bar);
+    if (bytes) bulk_g2s(smem_u32(gs.buf[k]), p.pages + (uint64_t)id * kPartPage, bytes, bar);
 }
 
-// Sort this CTA's pages of bucket b by owner, in place, and record each
-// page's owner run offsets (its row of idx). Page copies run one ahead of the
-// sort; `seq` counts the CTA's pages over all buckets (buffer and phase).
-__device__ __forceinline__ bool sort_pages(const PartDev &p, const ColdSmem &s, uint32_t b, uint32_t &seq, uint32_t *s_warp,
-                           uint32_t *status) {
-    const uint32_t G = p.g_cold, tid = threadIdx.x;
+// This group's share of the CTA's pages of bucket b, each sorted by owner in
+// place with its owner run offsets recorded (its row of idx). `seq` counts
+// the group's pages over all buckets (buffer and phase). Returns false when
+// a page copy's wait ran out.
+template <int GROUPS>
+__device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t &seq,
+                                           uint32_t *status) {
+    const uint32_t G = p.g_cold, tid = threadIdx.x % kGroupThreads;
     const uint32_t bmask = (1u << p.cb_shift) - 1u;
-    const uint32_t j0 = p.bucket_pg[b] + blockIdx.x, j1 = p.bucket_pg[b + 1];
-    if (tid == 0 && j0 < j1) issue_page(p, s, j0, seq & 1u);
-    bool ok = true;
-    for (uint32_t j = j0; j < j1; j += gridDim.x, ++seq) {
+    const uint32_t stride = GROUPS * gridDim.x;
+    const uint32_t j0 = p.bucket_pg[b] + blockIdx.x + gs.g * gridDim.x, j1 = p.bucket_pg[b + 1];
+    if (tid == 0 && j0 < j1) issue_page(p, gs, j0, seq & 1u);
+    for (uint32_t j = j0; j < j1; j += stride, ++seq) {
         const uint32_t k = seq & 1u;
-        if (tid == 0 && j + gridDim.x < j1) issue_page(p, s, j + gridDim.x, k ^ 1u);
+        if (tid == 0 && j + stride < j1) issue_page(p, gs, j + stride, k ^ 1u);
         // bounded wait for this page's copy (phase = uses of buffer k so far)
-        ok = mbar_wait(smem_u32(s.bar + k), (seq >> 1) & 1u);
-        if (!__syncthreads_and(ok)) {
+        if (!mbar_wait(smem_u32(gs.bar + k), (seq >> 1) & 1u)) *reinterpret_cast<volatile uint32_t *>(gs.s_flag) = 1;
+        group_sync(gs.g);
+        if (*reinterpret_cast<volatile uint32_t *>(gs.s_flag)) {
             if (tid == 0) {
                 latch_status(status, SINET_ERR_TIMEOUT);
                 // the next page's copy, if one was issued, lands before the CTA ends
-                if (j + gridDim.x < j1) mbar_wait(smem_u32(s.bar + (k ^ 1u)), ((seq + 1) >> 1) & 1u);
+                if (j + stride < j1) mbar_wait(smem_u32(gs.bar + (k ^ 1u)), ((seq + 1) >> 1) & 1u);
             }
-            ok = false;
-            break;
+            return false;
         }
-        const uint32_t id = s.s_id[k], fill = s.s_fill[k];
-        const uint64_t *src = s.buf[k];
-        for (uint32_t o = tid; o <= G; o += blockDim.x) s.ocnt[o] = 0;
-        __syncthreads();
-        constexpr int U = kPartPage / kPartColdThreads;
+        const uint32_t id = gs.s_id[k], fill = gs.s_fill[k];
+        const uint64_t *src = gs.buf[k];
+        for (uint32_t o = tid; o <= G; o += kGroupThreads) gs.ocnt[o] = 0;
+        group_sync(gs.g);
+        constexpr int U = kPartPage / kGroupThreads;
         uint32_t own[U], rk[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint32_t e = tid + (uint32_t)u * kPartColdThreads;
+            const uint32_t e = tid + (uint32_t)u * kGroupThreads;
             own[u] = rk[u] = 0;
             if (e < fill) {
                 const uint32_t bin = (uint32_t)(src[e] >> 33);
                 own[u] = (uint32_t)divide(bin & bmask, p.own_div);
-                rk[u] = atomicAdd(s.ocnt + own[u], 1u);
+                rk[u] = atomicAdd(gs.ocnt + own[u], 1u);
             }
         }
-        __syncthreads();
-        scan_owners(s.ocnt, G, s_warp);
-        __syncthreads();
+        group_sync(gs.g);
+        // exclusive scan of the owner counts (4 per thread), total at ocnt[G]
+        {
+            const uint32_t i0 = 4 * tid;
+            uint32_t v[4], sum = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = i0 + u < G ? gs.ocnt[i0 + u] : 0u;
+                sum += v[u];
+            }
+            uint32_t total;
+            uint32_t ex = group_scan(sum, gs, &total);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (i0 + u < G) gs.ocnt[i0 + u] = ex;
+                ex += v[u];
+            }
+            if (tid == 0) gs.ocnt[G] = total;
+        }
+        group_sync(gs.g);
         uint16_t *row = p.idx + (uint64_t)j * (G + 1);
-        for (uint32_t o = tid; o <= G; o += blockDim.x) row[o] = (uint16_t)s.ocnt[o];
+        for (uint32_t o = tid; o <= G; o += kGroupThreads) row[o] = (uint16_t)gs.ocnt[o];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint32_t e = tid + (uint32_t)u * kPartColdThreads;
-            if (e < fill) s.srt[s.ocnt[own[u]] + rk[u]] = src[e];
+            const uint32_t e = tid + (uint32_t)u * kGroupThreads;
+            if (e < fill) gs.srt[gs.ocnt[own[u]] + rk[u]] = src[e];
         }
-        __syncthreads();
+        group_sync(gs.g);
         // back in place, 16 bytes per store
         uint4 *dst = reinterpret_cast<uint4 *>(p.pages + (uint64_t)id * kPartPage);
-        const uint4 *v = reinterpret_cast<const uint4 *>(s.srt);
-        for (uint32_t e = tid; 2 * e < fill; e += blockDim.x) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(gs.srt);
+        for (uint32_t e = tid; 2 * e < fill; e += kGroupThreads) {
             if (2 * e + 1 < fill) {
                 dst[e] = v[e];
             } else {
-                p.pages[(uint64_t)id * kPartPage + 2 * e] = s.srt[2 * e];
+                p.pages[(uint64_t)id * kPartPage + 2 * e] = gs.srt[2 * e];
             }
         }
-        __syncthreads();
+        group_sync(gs.g);
     }
-    // a copy issued for a page past the loop (none: the loop issues only
-    // pages it will take) is never left in flight
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        atomicAdd(p.p1_done + b, 1u);
-    }
-    return ok;
+    return true;
 }
+
+struct ReduceSmem {
+    uint32_t *rpid;  // [kRunChunk] run table: page id,
+    uint32_t *rbeg;  //   first entry of this owner's run in the page,
+    uint32_t *rpre;  //   [kRunChunk + 1] prefix of the runs' lengths
+    uint32_t *tile;  // [6][own_bins]: counts d0, d1; byte sums low d0, d1; high d0, d1
+};
 
 // Sum this CTA's bins of bucket b from every page's run, then store them.
 // The runs are staged in shared memory kRunChunk pages at a time (empty runs
 // left out); each warp then walks a contiguous stretch of the concatenated
 // runs 32 entries per step, four steps of loads in flight.
-__device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &p, const ColdSmem &s, uint32_t b,
-                              uint32_t accumulate, uint32_t *s_ok, uint32_t *s_warp, uint32_t *status) {
+__device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &p, const ReduceSmem &s, uint32_t b,
+                                              uint32_t accumulate, uint32_t *s_ok, uint32_t *s_warp,
+                                              uint32_t *status) {
     const uint32_t G = p.g_cold, T = p.own_bins, tid = threadIdx.x, o = blockIdx.x;
     if (tid == 0) {
         bool ok = false;
@@ -720,30 +749,26 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
     const uint32_t warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
     for (uint32_t c0 = p.bucket_pg[b]; c0 < p.bucket_pg[b + 1]; c0 += kRunChunk) {
         const uint32_t cn = min(kRunChunk, p.bucket_pg[b + 1] - c0);
-        // stage the non-empty runs: 4 pages per thread
-        constexpr int V = kRunChunk / kPartColdThreads;
-        uint32_t id[V], e0[V], len[V], nonempty = 0;
+        // stage the non-empty runs (one or two pages per thread)
+        uint32_t id[2] = {0, 0}, e0[2] = {0, 0}, len[2] = {0, 0}, nonempty = 0, mylen = 0;
+        const uint32_t per = (kRunChunk + blockDim.x - 1) / blockDim.x;  // pages per thread: 1 or 2
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t i = tid * V + (uint32_t)v;
-            id[v] = e0[v] = len[v] = 0;
-            if (i < cn) {
+        for (int v = 0; v < 2; ++v) {
+            const uint32_t i = tid * per + (uint32_t)v;
+            if ((uint32_t)v < per && i < cn) {
                 const uint16_t *row = p.idx + (uint64_t)(c0 + i) * (G + 1);
                 e0[v] = row[o];
                 len[v] = row[o + 1] - e0[v];
                 if (len[v]) id[v] = p.page_list[c0 + i];
             }
             nonempty += len[v] ? 1u : 0u;
+            mylen += len[v];
         }
-        uint32_t n_runs;
+        uint32_t n_runs, total;
         uint32_t pos = block_scan(nonempty, s_warp, &n_runs);
-        uint32_t mylen = 0;
-#pragma unroll
-        for (int v = 0; v < V; ++v) mylen += len[v];
-        uint32_t total;
         uint32_t epos = block_scan(mylen, s_warp, &total);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
+        for (int v = 0; v < 2; ++v) {
             if (!len[v]) continue;
             s.rpid[pos] = id[v];
             s.rbeg[pos] = e0[v];
@@ -754,8 +779,8 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
         if (tid == 0) s.rpre[n_runs] = total;
         __syncthreads();
         // this warp's stretch of the runs' entries
-        const uint32_t per = ((total + nw - 1) / nw + 31) & ~31u;
-        const uint32_t k0 = min(total, warp * per), k1 = min(total, k0 + per);
+        const uint32_t span = ((total + nw - 1) / nw + 31) & ~31u;
+        const uint32_t k0 = min(total, warp * span), k1 = min(total, k0 + span);
         uint32_t r = 0;
         if (k0 < k1) {  // first run holding entry k0: the last with rpre <= k0
             uint32_t lo = 0, n = n_runs;
@@ -824,38 +849,69 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
     return true;
 }
 
+// Both groups sort their share of bucket b's pages, then the bucket counts
+// this CTA as done.
+template <int GROUPS>
+__device__ __forceinline__ bool sort_bucket(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t &seq,
+                                            uint32_t *s_fail, uint32_t *status) {
+    if (!sort_pages<GROUPS>(p, gs, b, seq, status)) *reinterpret_cast<volatile uint32_t *>(s_fail) = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(p.p1_done + b, 1u);
+    }
+    return *reinterpret_cast<volatile uint32_t *>(s_fail) == 0;
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kPartColdThreads, 1) k_part_cold(HistArgs h, PartDev p, uint32_t accumulate,
-                                                                   uint32_t *status) {
+// Shared memory of the cold pass: GROUPS page-sorting groups, the run table,
+// the tile.
+__host__ __device__ constexpr size_t cold_group_bytes() { return 24ull * kPartPage; }
+
+template <int GROUPS>
+__global__ void __launch_bounds__(GROUPS * 512, 1) k_part_cold(HistArgs h, PartDev p, uint32_t accumulate,
+                                                               uint32_t *status) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_ok, s_id[2], s_fill[2];
-    __shared__ uint64_t s_bar[2];
-    ColdSmem s;
-    s.buf[0] = reinterpret_cast<uint64_t *>(smem);
-    s.buf[1] = s.buf[0] + kPartPage;
-    s.srt = s.buf[1] + kPartPage;
-    s.rpid = reinterpret_cast<uint32_t *>(s.srt + kPartPage);
-    s.rbeg = s.rpid + kRunChunk;
-    s.rpre = s.rbeg + kRunChunk;
-    s.ocnt = s.rpre + kRunChunk + 4;
-    s.tile = s.ocnt + ((p.g_cold + 1 + 3) & ~3u);
-    s.bar = s_bar;
-    s.s_id = s_id;
-    s.s_fill = s_fill;
+    __shared__ uint32_t s_gwarp[GROUPS][16];
+    __shared__ uint32_t s_ok, s_fail, s_gflag[GROUPS], s_id[GROUPS][2], s_fill[GROUPS][2];
+    __shared__ uint64_t s_bar[GROUPS][2];
+    const uint32_t g = threadIdx.x / kGroupThreads;
+    const size_t ocnt_words = (p.g_cold + 1 + 3) & ~3u;
+    GroupSmem gs;
+    uint8_t *gbase = smem + g * (cold_group_bytes() + 4 * ocnt_words);
+    gs.buf[0] = reinterpret_cast<uint64_t *>(gbase);
+    gs.buf[1] = gs.buf[0] + kPartPage;
+    gs.srt = gs.buf[1] + kPartPage;
+    gs.ocnt = reinterpret_cast<uint32_t *>(gs.srt + kPartPage);
+    gs.bar = s_bar[g];
+    gs.s_id = s_id[g];
+    gs.s_fill = s_fill[g];
+    gs.s_warp = s_gwarp[g];
+    gs.s_flag = &s_gflag[g];
+    gs.g = g;
+    ReduceSmem rs;
+    rs.rpid = reinterpret_cast<uint32_t *>(smem + GROUPS * (cold_group_bytes() + 4 * ocnt_words));
+    rs.rbeg = rs.rpid + kRunChunk;
+    rs.rpre = rs.rbeg + kRunChunk;
+    rs.tile = rs.rpre + kRunChunk + 4;
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&s_bar[0]), 1);
-        mbar_init(smem_u32(&s_bar[1]), 1);
+        for (int k = 0; k < GROUPS; ++k) {
+            mbar_init(smem_u32(&s_bar[k][0]), 1);
+            mbar_init(smem_u32(&s_bar[k][1]), 1);
+            s_gflag[k] = 0;
+        }
+        s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (p.n_buckets == 0) return;
     uint32_t seq = 0;
-    if (!sort_pages(p, s, 0, seq, s_warp, status)) return;
+    if (!sort_bucket<GROUPS>(p, gs, 0, seq, &s_fail, status)) return;
     for (uint32_t b = 0; b < p.n_buckets; ++b) {
-        if (b + 1 < p.n_buckets && !sort_pages(p, s, b + 1, seq, s_warp, status)) return;
-        if (!reduce_bucket(h, p, s, b, accumulate, &s_ok, s_warp, status)) return;
+        if (b + 1 < p.n_buckets && !sort_bucket<GROUPS>(p, gs, b + 1, seq, &s_fail, status)) return;
+        if (!reduce_bucket(h, p, rs, b, accumulate, &s_ok, s_warp, status)) return;
     }
 }
 
@@ -905,15 +961,18 @@ cudaError_t plan_partition(int lk, uint32_t table_smem, const RecArgs &r, const 
     const uint64_t routed_max = n * (h.two_dir ? 2ull : 1ull);
     if (routed_max >= 0xFFFFF000ull) return cudaErrorNotSupported;  // u32 positions and fills
     const uint32_t G = (uint32_t)sm_count;
-    if (G > 2 * kPartColdThreads) return cudaErrorNotSupported;
+    if (G > 2048) return cudaErrorNotSupported;  // four owner counts per thread of a 512-thread group
     // buckets: 2^cb bins each, at most kPartMaxBuckets of them; owners of G bins slices
     uint32_t cb = bucket_bits ? bucket_bits : 19u;
     while (cb < 31 && (((uint64_t)h.n_bins + (1ull << cb) - 1) >> cb) > kPartMaxBuckets) ++cb;
     const uint32_t nb = (uint32_t)(((uint64_t)h.n_bins + (1ull << cb) - 1) >> cb);
     const uint32_t T = (uint32_t)(((1ull << cb) + G - 1) / G);
-    const size_t cold_fixed = 24ull * kPartPage + 12ull * kRunChunk + 16 + 4ull * ((G + 1 + 3) & ~3u);
-    P.smem_cold = cold_fixed + 24ull * T;
-    if (P.smem_cold + 1024 > smem_optin) return cudaErrorNotSupported;
+    // two page-sorting groups where the tile leaves room, else one
+    const size_t group = cold_group_bytes() + 4ull * ((G + 1 + 3) & ~3u);
+    const size_t tail = 12ull * kRunChunk + 16 + 24ull * T;
+    P.cold_groups = 2 * group + tail + 2048 <= smem_optin ? 2 : 1;
+    P.smem_cold = P.cold_groups * group + tail;
+    if (P.smem_cold + 2048 > smem_optin) return cudaErrorNotSupported;
     // hot table: as many sets as shared memory allows (at least 2^4)
     const uint32_t tsm = (table_smem + 127u) & ~127u;
     uint32_t sb = 12;
@@ -1069,13 +1128,19 @@ cudaError_t run_partition(int lk, const RecArgs &r, const TableArgs &t, const Hi
     k_part_scan_pages<<<1, kPartMaxBuckets, 0, c.stream>>>(P.d);
     k_part_list_pages<<<2 * P.grid_main, 256, 0, c.stream>>>(P.d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = set_smem(k_part_cold, P.smem_cold)) != cudaSuccess) return e;
     uint32_t acc = accumulate ? 1u : 0u;
     HistArgs hh = h;
     uint32_t *status = c.status;
     void *args[] = {&hh, &d, &acc, &status};
-    e = cudaLaunchCooperativeKernel((const void *)k_part_cold, dim3(P.grid_cold), dim3(kPartColdThreads), args,
-                                    P.smem_cold, c.stream);
+    if (P.cold_groups == 2) {
+        if ((e = set_smem(k_part_cold<2>, P.smem_cold)) != cudaSuccess) return e;
+        e = cudaLaunchCooperativeKernel((const void *)k_part_cold<2>, dim3(P.grid_cold), dim3(1024), args,
+                                        P.smem_cold, c.stream);
+    } else {
+        if ((e = set_smem(k_part_cold<1>, P.smem_cold)) != cudaSuccess) return e;
+        e = cudaLaunchCooperativeKernel((const void *)k_part_cold<1>, dim3(P.grid_cold), dim3(512), args,
+                                        P.smem_cold, c.stream);
+    }
     if (e != cudaSuccess) return e;
     k_part_hot_add<<<std::max<uint32_t>(1, P.slots / 256), 256, 0, c.stream>>>(h, P.d, P.slots);
     return cudaGetLastError();

@@ -24,18 +24,20 @@
 
 namespace sinet {
 
-constexpr int kPartConsumers = 512;                 // consumer threads of the main pass
+// Main pass: 31 consumer warps and one producer warp, 1,024 threads (64
+// registers each fit the register file), one record per consumer per stage.
+constexpr int kPartConsumers = 992;                 // consumer threads of the main pass
 constexpr int kPartThreads = kPartConsumers + 32;   // plus one producer warp (TMA)
-constexpr uint32_t kPartStageRecords = 1024;        // records per TMA stage
-constexpr int kPartRPT = kPartStageRecords / kPartConsumers;  // records per consumer per stage (1 or 2)
+constexpr int kPartRPT = 1;                         // records per consumer per stage (1 or 2)
+constexpr uint32_t kPartStageRecords = kPartRPT * kPartConsumers;  // records per TMA stage
 static_assert(kPartRPT == 1 || kPartRPT == 2, "one or two records per consumer thread and stage");
+static_assert((4 * kPartStageRecords) % 16 == 0, "every stage starts 16-byte aligned in every stream");
 constexpr uint32_t kPartStages = 4;
 constexpr uint32_t kPartStageBytes = 20 * kPartStageRecords;
 constexpr uint32_t kPartPageBits = 11;              // 2,048 entries (16 KB) per page
 constexpr uint32_t kPartPage = 1u << kPartPageBits;
 constexpr uint32_t kPartMaxBuckets = 256;
 constexpr uint32_t kPartMaxCand = 16384;            // hot candidates taken from the sample
-constexpr int kPartColdThreads = 512;
 constexpr uint32_t kPartSampleChunk = 512;          // records per sampled chunk
 constexpr uint32_t kPartSampleSetBits = 9;          // sample pass: per-CTA pre-aggregation cache
 
@@ -85,6 +87,7 @@ struct PartPlan {
     PartDev d;                 // pointers filled once the scratch exists
     uint32_t slots;            // 4 << set_bits
     int grid_main, grid_sample, grid_cold;
+    int cold_groups;           // page-sorting groups of 512 threads in a cold-pass CTA (1 or 2)
     size_t smem_main, smem_sample, smem_cold;
     size_t scratch_bytes;
     // scratch layout (byte offsets)

@@ -33,12 +33,16 @@ def _widths():
 def _case(t0, w, n_bins, rng):
     span = n_bins * w
     rel = [0, 1, w - 1, w, w + 1, span - w, span - w - 1, span - 1, span, span + 1]
-    rel += [int(x) for x in rng.integers(0, span, 200, dtype=np.uint64)]
-    rel += [(q * w + r) for q in rng.integers(0, n_bins, 50) for r in (0, w - 1)]
+    hi_, lo_ = rng.integers(0, 1 << 32, 200), rng.integers(0, 1 << 32, 200)
+    rel += [(int(a) << 32 | int(b)) % span for a, b in zip(hi_, lo_)]
+    rel += [(int(q) * w + r) for q in rng.integers(0, n_bins, 50) for r in (0, w - 1)]
     rel = [r for r in rel if 0 <= r < (1 << 64) - t0] + [-1, -w]  # and before t0 (wraps)
-    ts = np.array([(t0 + r) % (1 << 64) for r in rel], np.uint64)
-    want = np.array([(int(x) - t0) // w if t0 <= int(x) < t0 + span else NONE for x in ts], np.uint64)
-    return ts, want.astype(np.uint32)
+    vals = [(t0 + r) % (1 << 64) for r in rel]
+    # built from 32-bit halves: Python ints of 2^63 and above do not convert directly
+    ts = (np.array([v >> 32 for v in vals], np.uint64) << np.uint64(32)) | np.array(
+        [v & 0xFFFFFFFF for v in vals], np.uint64)
+    want = np.array([(v - t0) // w if t0 <= v < t0 + span else NONE for v in vals], np.uint32)
+    return ts, want
 
 
 @pytest.mark.parametrize("t0_kind", ["zero", "mid", "near_top"])
