@@ -182,6 +182,7 @@ KERNEL_SOURCES = {
     "k_fused_tile": ["fused.cu", "combine.cuh", "launch.h", "records.cuh", "common.cuh"],
     "k_fused_atomic": ["fused.cu", "combine.cuh", "launch.h", "records.cuh", "common.cuh"],
     "k_fused_owner": ["owner.cu", "owner.h", "launch.h", "records.cuh", "common.cuh"],
+    "k_part_main": ["partition.cu", "partition.h", "combine.cuh", "launch.h", "records.cuh", "common.cuh"],
 }
 
 

@@ -85,7 +85,7 @@ typedef enum {
                                       512 threads per block. */
     SINET_STRAT_PARTITION = 8      /* hot/cold partition, for unsorted input over histograms far
                                       larger than L2 (Section 5's map-reduce with the reduction
-                                      kept on chip): a strided sample of about n / 256 records
+                                      kept on chip): a strided sample of about n / 2,048 records
                                       ranks the bins; the most sampled ones (up to 16,384 slots,
                                       as shared memory allows) are summed in shared memory by
                                       every CTA; every other routed update is appended as an
@@ -98,9 +98,11 @@ typedef enum {
                                       until there are at most 256 ranges; at most 2^20).
                                       sinet_discriminate_histogram only, no watch list; at most
                                       2^32 - 4,096 routed updates and 2^28 bins. Scratch, stream-
-                                      ordered: 16 bytes per routed update plus about 2.5 KB per
-                                      2,048-entry page for its bookkeeping, and 48 MB at most
-                                      for the sample. */
+                                      ordered: 16 KB pages of 2,048 entries for every routed
+                                      update (8 bytes each) plus two pages per CTA and range,
+                                      about 320 bytes of bookkeeping per page, and 64 MB at most
+                                      for the sample. The second kernel is a cooperative launch
+                                      (one CTA per SM, all resident). */
 } sinet_strategy;
 
 /* How membership is looked up. Both are exact. */
