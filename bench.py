@@ -1,15 +1,19 @@
-"""Benchmark: discriminate + millisecond-histogram one paper-scale day on GB300.
+"""Benchmark: discriminate + millisecond-histogram a paper-scale day on GB300.
 
-Default workload: 400 M time-sorted session records (diurnal 3:1 rate, +-500 ms
-jitter), 2,000 CIDR prefixes /8-/30, 1 ms bins over 24 h (86.4 M bins x 2
-directions). A step = zero the histogram + one fused discriminate/histogram
-pass over all records (inputs resident in HBM; 8 GB of records, far larger
-than L2). The plain discriminate -> radix sort -> reduce-by-key path is timed
-on the same data for comparison, and ``e2e`` times the same step through the
-public API with the records copied from pinned host memory and the histogram
-copied back every step.
+Default workload: the heavy day, 1.6 B unsorted session records whose bins
+and hosts are Zipf(1.1)-skewed, 8,000 CIDR prefixes /8-/32, 1 ms bins over
+24 h (86.4 M bins x 2 directions). A step = one fused discriminate/histogram
+call over all records (plus the output zeroing for the strategies that need
+it; inputs resident in HBM, 32 GB of records, far larger than L2). The
+strategy is picked by one timed run of each candidate. The plain
+discriminate -> radix sort -> reduce-by-key path is timed on the same data
+for comparison, ``e2e`` times the same step through the public API with the
+records copied from pinned host memory and the histogram copied back every
+step, and the 400 M-record time-sorted day (2,000 prefixes) is timed as a
+second line of figures under ``day``.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload day|heavy|tiny]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload heavy|day|tiny|batch|serve]
+                  [--shard replicas|records|time]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 Prints one JSON line (rank 0).

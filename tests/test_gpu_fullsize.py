@@ -1,7 +1,8 @@
 """Full-size parity at the benchmark's sizes and launch configurations: the
 day workload (400 M time-sorted records, 86.4 M bins) with the tile and
 owner-computes strategies, the heavy workload (1.6 B unsorted Zipf records) with the
-warp-combining atomic strategy, and the 256-slice batch (708 M records) with
+cell and hot/cold partition strategies (the two the benchmark's tuning picks
+between), and the 256-slice batch (708 M records) with
 the autotuner's choices. The oracle recomputes a sample of bins one by one
 (it scans every record and keeps only those bins): random bins, the window's
 edges and the hottest bins. Every output also meets the invariants that hold
@@ -76,7 +77,8 @@ def _check_sampled(orc, net, ln, rec, w, got, policy, seed, hot):
 
 @pytest.mark.parametrize("key,strategy,other,hot", [("day", "priv_tile", "global_atomic", (0, 500)),
                                                     ("day", "owner", "priv_tile", (0, 500)),
-                                                    ("heavy", "atomic_cell", "global_atomic", (1000, 1020))])
+                                                    ("heavy", "atomic_cell", "global_atomic", (1000, 1020)),
+                                                    ("heavy", "partition", "atomic_cell", (1000, 1020))])
 def test_full_workload(orc, key, strategy, other, hot):
     w = gen.WORKLOADS[key]
     net, ln, h = _pinned(w)
