@@ -256,9 +256,8 @@ struct MainSmem {
 // is needed: a thread holds at most one claimed position at a time, so the
 // claimed but unwritten positions (at most one per thread) stay within two
 // pages and a slot is never reused while a thread still needs it.
-__device__ __forceinline__ void cold_emit(const PartDev &p, const MainSmem &m, uint32_t key, uint32_t by,
-                                          uint32_t *status) {
-    const uint32_t bk = (key >> 1) >> p.cb_shift;
+__device__ __forceinline__ void cold_emit_entry(const PartDev &p, const MainSmem &m, uint64_t e, uint32_t *status) {
+    const uint32_t bk = (uint32_t)(e >> 33) >> p.cb_shift;
     const uint32_t pos = atomicAdd(m.cur + bk, 1u);
     const uint32_t pg = pos >> kPartPageBits, off = pos & (kPartPage - 1);
     volatile uint64_t *sl = m.slot + 4 * bk;
@@ -281,7 +280,12 @@ __device__ __forceinline__ void cold_emit(const PartDev &p, const MainSmem &m, u
         v = sl[pg & 3];
     }
     const uint32_t id = (uint32_t)v;
-    if (id < p.pages_cap) p.pages[(uint64_t)id * kPartPage + off] = (uint64_t)key << 32 | by;
+    if (id < p.pages_cap) p.pages[(uint64_t)id * kPartPage + off] = e;
+}
+
+__device__ __forceinline__ void cold_emit(const PartDev &p, const MainSmem &m, uint32_t key, uint32_t by,
+                                          uint32_t *status) {
+    cold_emit_entry(p, m, (uint64_t)key << 32 | by, status);
 }
 
 // One routed, in-window record: both directions share the bin's hot slot.
@@ -320,6 +324,48 @@ __device__ __forceinline__ void part_record(const HistArgs &h, const PartDev &p,
     const uint32_t bin = inw ? (W1 ? (uint32_t)rel : (uint32_t)divide(rel, h.div)) : 0u;
     const uint32_t dirs = dirs_of_packed(h, cls, inw, oorp);
     if (dirs) part_update(p, m, bin, dirs, by, status);
+}
+
+// The staged path's pieces, for two records per thread and warp-wide steps.
+
+// Hot-table slot of a bin, or kNoKey.
+__device__ __forceinline__ uint32_t hot_slot(const MainSmem &m, uint32_t bin) {
+    const uint32_t set = fib_hash(bin) >> m.shift;
+    const uint4 k4 = *reinterpret_cast<const uint4 *>(m.hkeys + 4 * set);
+    if (k4.x == bin && k4.w == bin) return 4 * set + (threadIdx.x & 3u);  // a replicated set
+    const int way = k4.x == bin ? 0 : k4.y == bin ? 1 : k4.z == bin ? 2 : k4.w == bin ? 3 : -1;
+    return way < 0 ? kNoKey : 4 * set + (uint32_t)way;
+}
+
+__device__ __forceinline__ void hot_add(const MainSmem &m, uint32_t slot, uint32_t d, uint32_t by) {
+    const uint32_t i = d * m.slots + slot;
+    atomicAdd(m.hcnt + i, 1u);
+    smem_add_wide(m.hlo + i, m.hhi + i, by, 0u);
+}
+
+// First direction of a routed record: outgoing when its class routes there.
+__device__ __forceinline__ uint32_t first_dir(uint32_t dirs) { return (dirs & 1u) ? 0u : 1u; }
+
+__device__ __forceinline__ uint64_t cold_entry(uint32_t bin, uint32_t d, uint32_t by) {
+    return (uint64_t)(bin << 1 | d) << 32 | by;
+}
+
+// Warp totals of 8-bit class counters and 16-bit out-of-window counters
+// into the CTA's counters.
+__device__ __forceinline__ void drain8(uint32_t &cc8, uint32_t &oorp, unsigned long long *s_cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t v = __reduce_add_sync(kFull, (cc8 >> (8 * k)) & 0xFFu);
+        if (lane == 0 && v) atomicAdd(s_cnt + k, (unsigned long long)v);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const uint32_t v = __reduce_add_sync(kFull, (oorp >> (16 * k)) & 0xFFFFu);
+        if (lane == 0 && v) atomicAdd(s_cnt + 4 + k, (unsigned long long)v);
+    }
+    cc8 = 0;
+    oorp = 0;
 }
 
 }  // namespace
@@ -414,15 +460,32 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
                 mbar_wait(smem_u32(&full_bar[k % kPartStages]), (uint32_t)(k / kPartStages) & 1u);
         }
     } else {
-        uint64_t ccp = 0;   // packed per-thread class counts
-        uint32_t oorp = 0;  // packed per-thread out-of-window counts
+        uint32_t cc8 = 0;   // per-thread class counts, 8-bit fields
+        uint32_t oorp = 0;  // per-thread out-of-window counts, 16-bit fields
         uint32_t since = 0;
-        for (uint64_t it = 0;; ++it) {
-            const uint64_t ch = blockIdx.x + it * gridDim.x;
-            if (ch >= p.n_full) break;
-            const uint32_t s = (uint32_t)(it % kPartStages);
-            bool ok = mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(it / kPartStages) & 1u);
-            ok = __all_sync(kFull, ok);
+        // two stages per iteration: record j of this thread comes from chunk q + j
+        for (uint64_t q = 0;; q += 2) {
+            const uint64_t ch0 = blockIdx.x + q * gridDim.x;
+            if (ch0 >= p.n_full) break;
+            const bool has1 = ch0 + gridDim.x < p.n_full;  // warp-uniform
+            uint64_t ts[2] = {0, 0};
+            uint32_t a[4] = {0, 0, 0, 0}, by[2] = {0, 0};
+            bool ok = true;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (j == 1 && !has1) break;
+                const uint64_t qq = q + (uint64_t)j;
+                const uint32_t s = (uint32_t)(qq % kPartStages);
+                ok = __all_sync(kFull, mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(qq / kPartStages) & 1u));
+                if (!ok) break;
+                const uint8_t *sp = stage + s * kPartStageBytes;
+                ts[j] = *reinterpret_cast<const uint64_t *>(sp + 8 * tid);
+                a[2 * j] = *reinterpret_cast<const uint32_t *>(sp + 8 * R + 4 * tid);
+                a[2 * j + 1] = *reinterpret_cast<const uint32_t *>(sp + 12 * R + 4 * tid);
+                by[j] = *reinterpret_cast<const uint32_t *>(sp + 16 * R + 4 * tid);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
+            }
             if (!ok) {
                 if (lane == 0) {
                     latch_status(status, SINET_ERR_TIMEOUT);
@@ -430,38 +493,63 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
                 }
                 break;
             }
-            const uint8_t *sp = stage + s * kPartStageBytes;
-            if (kPartRPT == 2) {
-                const ulonglong2 ts2 = *reinterpret_cast<const ulonglong2 *>(sp + 16 * tid);
-                const uint2 s2 = *reinterpret_cast<const uint2 *>(sp + 8 * R + 8 * tid);
-                const uint2 d2 = *reinterpret_cast<const uint2 *>(sp + 12 * R + 8 * tid);
-                const uint2 b2 = *reinterpret_cast<const uint2 *>(sp + 16 * R + 8 * tid);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
-                uint32_t a[2] = {s2.x, s2.y}, in_s[2], in_d[2];
-                C.template in_n<2>(a, in_s);
-                a[0] = d2.x;
-                a[1] = d2.y;
-                C.template in_n<2>(a, in_d);
-                part_record<W1>(h, p, m, ts2.x, b2.x, in_s[0] | in_d[0] << 1, ccp, oorp, status);
-                part_record<W1>(h, p, m, ts2.y, b2.y, in_s[1] | in_d[1] << 1, ccp, oorp, status);
-            } else {
-                const uint64_t ts1 = *reinterpret_cast<const uint64_t *>(sp + 8 * tid);
-                const uint32_t s1 = *reinterpret_cast<const uint32_t *>(sp + 8 * R + 4 * tid);
-                const uint32_t d1 = *reinterpret_cast<const uint32_t *>(sp + 12 * R + 4 * tid);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(sp + 16 * R + 4 * tid);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
-                uint32_t a[2] = {s1, d1}, in_a[2];
-                C.template in_n<2>(a, in_a);
-                part_record<W1>(h, p, m, ts1, b1, in_a[0] | in_a[1] << 1, ccp, oorp, status);
+            uint32_t in[4];
+            C.template in_n<4>(a, in);
+            uint32_t bin[2], dirs[2], slot[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const bool valid = j == 0 || has1;
+                const uint32_t cls = in[2 * j] | in[2 * j + 1] << 1;
+                if (valid) cc8 += 1u << (8 * cls);
+                const uint64_t rel = ts[j] - h.t0;
+                const bool inw = rel < h.span;
+                bin[j] = inw ? (W1 ? (uint32_t)rel : (uint32_t)divide(rel, h.div)) : 0u;
+                uint32_t d = valid ? (h.policy >> (8 * cls)) & 3u : 0u;
+                if (!inw) {
+                    oorp += (d & 1u) | ((d >> 1) << 16);
+                    d = 0;
+                }
+                dirs[j] = d;
+                slot[j] = d ? hot_slot(m, bin[j]) : kNoKey;
             }
-            // at most two records per thread per stage: drain well before a 16-bit field fills
-            if (++since == 16384) {
-                drain_packed(ccp, oorp, s_cnt);
+            // hot bins, first direction: one shared-memory add per record
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (slot[j] != kNoKey) hot_add(m, slot[j], first_dir(dirs[j]), by[j]);
+            // classes routed to both directions: the second one
+            if (__any_sync(kFull, dirs[0] == 3u || dirs[1] == 3u)) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (dirs[j] != 3u) continue;
+                    if (slot[j] != kNoKey) hot_add(m, slot[j], 1u, by[j]);
+                    else cold_emit_entry(p, m, cold_entry(bin[j], 1u, by[j]), status);
+                }
+            }
+            // cold bins, first direction: the warp's entries gathered onto its
+            // lanes, so the append runs once per 32 entries
+            const bool c0 = dirs[0] && slot[0] == kNoKey, c1 = dirs[1] && slot[1] == kNoKey;
+            const uint32_t m0 = __ballot_sync(kFull, c0), m1 = __ballot_sync(kFull, c1);
+            const uint32_t n0 = __popc(m0), n = n0 + __popc(m1);
+            if (n) {
+                const uint64_t e0 = cold_entry(bin[0], first_dir(dirs[0]), by[0]);
+                const uint64_t e1 = cold_entry(bin[1], first_dir(dirs[1]), by[1]);
+                for (uint32_t base = 0; base < n; base += 32) {
+                    const uint32_t g = base + lane;
+                    const bool second = g >= n0;
+                    const uint32_t local = second ? g - n0 : g;
+                    const uint32_t src = g < n ? __fns(second ? m1 : m0, 0, (int)local + 1) : 0u;
+                    const uint64_t v0 = __shfl_sync(kFull, e0, (int)src);
+                    const uint64_t v1 = __shfl_sync(kFull, e1, (int)src);
+                    if (g < n) cold_emit_entry(p, m, second ? v1 : v0, status);
+                }
+            }
+            // at most two records per field per iteration: drain before 8 bits fill
+            if (++since == 127) {
+                drain8(cc8, oorp, s_cnt);
                 since = 0;
             }
         }
+        uint64_t ccp = 0;  // the records outside the staged chunks: 16-bit class fields
         // records outside the staged chunks, one by one
         const uint64_t tail_lo = p.i_lo + p.n_full * R;
         const uint64_t n_scalar = p.n_head + (r.g.n - tail_lo);
@@ -476,6 +564,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
         }
         __syncwarp();
         drain_packed(ccp, oorp, s_cnt);
+        drain8(cc8, oorp, s_cnt);
     }
     __syncthreads();
 
