@@ -370,10 +370,10 @@ __device__ __forceinline__ void drain8(uint32_t &cc8, uint32_t &oorp, unsigned l
 
 }  // namespace
 
-// One CTA per SM: warp 16 issues TMA bulk copies of stage after stage (a
+// One CTA per SM: warp 31 issues TMA bulk copies of stage after stage (a
 // chunk of kPartStageRecords records of each stream: ts, src, dst, bytes);
-// warps 0-15 take two records per thread from each stage, release the stage,
-// and classify, bin and update. Chunks go to CTAs round-robin.
+// warps 0-30 take one record per thread from each of two stages, release
+// them, and classify, bin and update. Chunks go to CTAs round-robin.
 template <int LK, bool W1>
 __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableArgs t, HistArgs h, PartDev p,
                                                                uint32_t *status) {
@@ -525,24 +525,12 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
                     else cold_emit_entry(p, m, cold_entry(bin[j], 1u, by[j]), status);
                 }
             }
-            // cold bins, first direction: the warp's entries gathered onto its
-            // lanes, so the append runs once per 32 entries
-            const bool c0 = dirs[0] && slot[0] == kNoKey, c1 = dirs[1] && slot[1] == kNoKey;
-            const uint32_t m0 = __ballot_sync(kFull, c0), m1 = __ballot_sync(kFull, c1);
-            const uint32_t n0 = __popc(m0), n = n0 + __popc(m1);
-            if (n) {
-                const uint64_t e0 = cold_entry(bin[0], first_dir(dirs[0]), by[0]);
-                const uint64_t e1 = cold_entry(bin[1], first_dir(dirs[1]), by[1]);
-                for (uint32_t base = 0; base < n; base += 32) {
-                    const uint32_t g = base + lane;
-                    const bool second = g >= n0;
-                    const uint32_t local = second ? g - n0 : g;
-                    const uint32_t src = g < n ? __fns(second ? m1 : m0, 0, (int)local + 1) : 0u;
-                    const uint64_t v0 = __shfl_sync(kFull, e0, (int)src);
-                    const uint64_t v1 = __shfl_sync(kFull, e1, (int)src);
-                    if (g < n) cold_emit_entry(p, m, second ? v1 : v0, status);
-                }
-            }
+            // cold bins, first direction: each lane appends its own entries (a
+            // gather of the warp's entries onto its lanes first costs more
+            // instructions than the second append it saves)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (dirs[j] && slot[j] == kNoKey) cold_emit_entry(p, m, cold_entry(bin[j], first_dir(dirs[j]), by[j]), status);
             // at most two records per field per iteration: drain before 8 bits fill
             if (++since == 127) {
                 drain8(cc8, oorp, s_cnt);
@@ -640,66 +628,47 @@ __global__ void __launch_bounds__(256) k_part_list_pages(PartDev p) {
 // 5. Cold pass (cooperative: every CTA resident). CTA o owns bins
 // [o * own_bins, (o + 1) * own_bins) of every bucket. For each bucket b in
 // turn: sort_pages(b + 1), then reduce(b): the pages of the next bucket are
-// sorted while the other CTAs finish this one.
+// sorted while the other CTAs finish this one. A bucket's pages are handed
+// out one at a time from a per-bucket cursor to whichever page-sorting group
+// asks next, so every group ends its share of a bucket at about the same time.
 
 namespace {
 
-constexpr uint32_t kRunChunk = 1024;      // pages whose runs one staging of the run table covers
-constexpr uint32_t kGroupThreads = 512;   // threads of one page-sorting group
+constexpr uint32_t kRunChunk = 1024;     // pages whose runs one staging of the run table covers
+constexpr uint32_t kColdThreads = 1024;  // threads of a cold-pass CTA (GROUPS page-sorting groups)
 
-// One page-sorting group's shared state: two page buffers (a copy of the next
-// page lands while this one is sorted), the sorted page, owner counts.
+// One page-sorting group's shared state: two page buffers (the copy of the
+// next page lands in one while the page in the other is sorted in place) and
+// the owner counts of each.
 struct GroupSmem {
-    uint64_t *buf[2];  // [kPartPage]
-    uint64_t *srt;     // [kPartPage]
-    uint32_t *ocnt;    // [g_cold + 1]
-    uint64_t *bar;     // [2] page copies
-    uint32_t *s_id;    // [2] page id of the copy in flight into buf[k]
-    uint32_t *s_fill;  // [2] its entries
-    uint32_t *s_warp;  // [16] scan partials
-    uint32_t *s_flag;  // a wait that ran out
-    uint32_t g;        // group index (named barrier 1 + g)
+    uint64_t *buf[2];   // [kPartPage]
+    uint32_t *ocnt[2];  // [cold_ocnt_words] owner counts, then run offsets
+    uint64_t *bar;      // [2] page copies
+    uint32_t *s_id;     // [2] page id of the copy in flight into buf[k]
+    uint32_t *s_fill;   // [2] its entries
+    uint32_t *s_next;   // list position of the group's next page
+    uint32_t *s_flag;   // a wait that ran out
+    uint32_t g;         // group index (named barrier 1 + g)
 };
 
+template <int GROUPS>
 __device__ __forceinline__ void group_sync(uint32_t g) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
-}
-
-// Group-wide exclusive scan of v (one value per thread of the group).
-__device__ __forceinline__ uint32_t group_scan(uint32_t v, const GroupSmem &gs, uint32_t *total) {
-    const uint32_t t = threadIdx.x % kGroupThreads;
-    const uint32_t lane = t & 31, warp = t >> 5;
-    uint32_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-    }
-    group_sync(gs.g);
-    if (lane == 31) gs.s_warp[warp] = incl;
-    group_sync(gs.g);
-    uint32_t woff = 0, tot = 0;
-    for (uint32_t w = 0; w < kGroupThreads / 32; ++w) {
-        if (w < warp) woff += gs.s_warp[w];
-        tot += gs.s_warp[w];
-    }
-    *total = tot;
-    return woff + incl - v;
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kColdThreads / GROUPS) : "memory");
 }
 
 // Block-wide exclusive scan of v (one value per thread of the whole CTA).
-__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+__device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t *s_warp, uint64_t *total) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t incl = v;
+    uint64_t incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        const uint64_t y = __shfl_up_sync(kFull, incl, o);
         if (lane >= (uint32_t)o) incl += y;
     }
     __syncthreads();
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    uint32_t woff = 0, t = 0;
+    uint64_t woff = 0, t = 0;
     for (uint32_t w = 0; w < nw; ++w) {
         if (w < warp) woff += s_warp[w];
         t += s_warp[w];
@@ -716,93 +685,114 @@ __device__ __forceinline__ void issue_page(const PartDev &p, const GroupSmem &gs
     gs.s_fill[k] = fill;
     const uint32_t bytes = (fill * 8u + 15u) & ~15u;  // within the 16 KB page
     const uint32_t bar = smem_u32(gs.bar + k);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of buf[k] first
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier accesses of buf[k] first
     mbar_expect_tx(bar, bytes);
     if (bytes) bulk_g2s(smem_u32(gs.buf[k]), p.pages + (uint64_t)id * kPartPage, bytes, bar);
 }
 
-// This group's share of the CTA's pages of bucket b, each sorted by owner in
-// place with its owner run offsets recorded (its row of idx). `seq` counts
-// the group's pages over all buckets (buffer and phase). Returns false when
-// a page copy's wait ran out.
+// The group's thread 0: claim bucket b's next unsorted page and start its
+// copy into buf[k]. Returns its list position (the bucket's end or beyond
+// when every page is taken).
+__device__ __forceinline__ uint32_t claim_page(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t k) {
+    const uint32_t j = p.bucket_pg[b] + atomicAdd(p.pg_next + b, 1u);
+    if (j < p.bucket_pg[b + 1]) issue_page(p, gs, j, k);
+    return j;
+}
+
+// This group's pages of bucket b, each sorted by owner in place with its
+// owner run offsets recorded (its row of idx), then the group counts itself
+// done with the bucket. Four group barriers per page: the copy has landed;
+// owners counted; offsets scanned; entries scattered (the copy of the next
+// page, into the other buffer, starts after the first). `seq` counts the
+// group's pages over all buckets (buffer and phase). Returns false when a
+// page copy's wait ran out.
 template <int GROUPS>
 __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t &seq,
                                            uint32_t *status) {
-    const uint32_t G = p.g_cold, tid = threadIdx.x % kGroupThreads;
-    const uint32_t bmask = (1u << p.cb_shift) - 1u;
-    const uint32_t stride = GROUPS * gridDim.x;
-    const uint32_t j0 = p.bucket_pg[b] + blockIdx.x + gs.g * gridDim.x, j1 = p.bucket_pg[b + 1];
-    if (tid == 0 && j0 < j1) issue_page(p, gs, j0, seq & 1u);
-    for (uint32_t j = j0; j < j1; j += stride, ++seq) {
+    constexpr uint32_t GT = kColdThreads / GROUPS;
+    constexpr int U = kPartPage / GT;
+    const uint32_t G = p.g_cold, tid = threadIdx.x % GT, lane = tid & 31;
+    const uint32_t bmask = (1u << p.cb_shift) - 1u, end = p.bucket_pg[b + 1];
+    volatile uint32_t *s_next = gs.s_next;
+    if (tid == 0) *s_next = claim_page(p, gs, b, seq & 1u);
+    group_sync<GROUPS>(gs.g);
+    for (uint32_t j = *s_next; j < end; ++seq) {
         const uint32_t k = seq & 1u;
-        if (tid == 0 && j + stride < j1) issue_page(p, gs, j + stride, k ^ 1u);
         // bounded wait for this page's copy (phase = uses of buffer k so far)
         if (!mbar_wait(smem_u32(gs.bar + k), (seq >> 1) & 1u)) *reinterpret_cast<volatile uint32_t *>(gs.s_flag) = 1;
-        group_sync(gs.g);
+        group_sync<GROUPS>(gs.g);
         if (*reinterpret_cast<volatile uint32_t *>(gs.s_flag)) {
-            if (tid == 0) {
-                latch_status(status, SINET_ERR_TIMEOUT);
-                // the next page's copy, if one was issued, lands before the CTA ends
-                if (j + stride < j1) mbar_wait(smem_u32(gs.bar + (k ^ 1u)), ((seq + 1) >> 1) & 1u);
-            }
+            if (tid == 0) latch_status(status, SINET_ERR_TIMEOUT);
             return false;
         }
+        // the other buffer's page was stored back before the barrier: the next copy may land there
+        if (tid == 0) *s_next = claim_page(p, gs, b, k ^ 1u);
         const uint32_t id = gs.s_id[k], fill = gs.s_fill[k];
-        const uint64_t *src = gs.buf[k];
-        for (uint32_t o = tid; o <= G; o += kGroupThreads) gs.ocnt[o] = 0;
-        group_sync(gs.g);
-        constexpr int U = kPartPage / kGroupThreads;
-        uint32_t own[U], rk[U];
+        uint64_t *pg = gs.buf[k];
+        uint32_t *oc = gs.ocnt[k];
+        uint64_t ent[U];
+        uint32_t pos[U];  // owner << 16 | rank among the owner's entries
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint32_t e = tid + (uint32_t)u * kGroupThreads;
-            own[u] = rk[u] = 0;
+            const uint32_t e = tid + (uint32_t)u * GT;
+            ent[u] = 0;
+            pos[u] = 0;
             if (e < fill) {
-                const uint32_t bin = (uint32_t)(src[e] >> 33);
-                own[u] = (uint32_t)divide(bin & bmask, p.own_div);
-                rk[u] = atomicAdd(gs.ocnt + own[u], 1u);
+                ent[u] = pg[e];
+                const uint32_t own = (uint32_t)divide((uint32_t)(ent[u] >> 33) & bmask, p.own_div);
+                pos[u] = own << 16 | atomicAdd(oc + own, 1u);
             }
         }
-        group_sync(gs.g);
-        // exclusive scan of the owner counts (4 per thread), total at ocnt[G]
-        {
-            const uint32_t i0 = 4 * tid;
-            uint32_t v[4], sum = 0;
+        // the next page's counts start from zero (the last page that used
+        // them wrote its row before the barrier above)
+        uint32_t *on = gs.ocnt[k ^ 1u];
+        for (uint32_t o = tid; o <= G; o += GT) on[o] = 0;
+        group_sync<GROUPS>(gs.g);
+        // exclusive scan of the G + 1 counts by the group's first warp (the
+        // last count is always zero, so its offset is the page's fill)
+        if (tid < 32) {
+            const uint32_t per = (G + 1 + 31) / 32, o0 = lane * per;
+            uint32_t sum = 0;
+            for (uint32_t q = 0; q < per; ++q)
+                if (o0 + q <= G) sum += oc[o0 + q];
+            uint32_t incl = sum;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                v[u] = i0 + u < G ? gs.ocnt[i0 + u] : 0u;
-                sum += v[u];
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, d);
+                if (lane >= (uint32_t)d) incl += y;
             }
-            uint32_t total;
-            uint32_t ex = group_scan(sum, gs, &total);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (i0 + u < G) gs.ocnt[i0 + u] = ex;
-                ex += v[u];
+            uint32_t ex = incl - sum;
+            for (uint32_t q = 0; q < per; ++q) {
+                if (o0 + q > G) break;
+                const uint32_t c = oc[o0 + q];
+                oc[o0 + q] = ex;
+                ex += c;
             }
-            if (tid == 0) gs.ocnt[G] = total;
         }
-        group_sync(gs.g);
+        group_sync<GROUPS>(gs.g);
+        // every entry is in registers: scatter them in place, owner by owner
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (tid + (uint32_t)u * GT < fill) pg[oc[pos[u] >> 16] + (pos[u] & 0xFFFFu)] = ent[u];
         uint16_t *row = p.idx + (uint64_t)j * (G + 1);
-        for (uint32_t o = tid; o <= G; o += kGroupThreads) row[o] = (uint16_t)gs.ocnt[o];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t e = tid + (uint32_t)u * kGroupThreads;
-            if (e < fill) gs.srt[gs.ocnt[own[u]] + rk[u]] = src[e];
-        }
-        group_sync(gs.g);
-        // back in place, 16 bytes per store
+        for (uint32_t o = tid; o <= G; o += GT) row[o] = (uint16_t)oc[o];
+        group_sync<GROUPS>(gs.g);
+        // back to the page, 16 bytes per store
         uint4 *dst = reinterpret_cast<uint4 *>(p.pages + (uint64_t)id * kPartPage);
-        const uint4 *v = reinterpret_cast<const uint4 *>(gs.srt);
-        for (uint32_t e = tid; 2 * e < fill; e += kGroupThreads) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(pg);
+        for (uint32_t e = tid; 2 * e < fill; e += GT) {
             if (2 * e + 1 < fill) {
                 dst[e] = v[e];
             } else {
-                p.pages[(uint64_t)id * kPartPage + 2 * e] = gs.srt[2 * e];
+                p.pages[(uint64_t)id * kPartPage + 2 * e] = pg[2 * e];
             }
         }
-        group_sync(gs.g);
+        j = *s_next;
     }
+    // the group's pages and rows are stored: count the group done with bucket b
+    __threadfence();
+    group_sync<GROUPS>(gs.g);
+    if (tid == 0) atomicAdd(p.p1_done + b, 1u);
     return true;
 }
 
@@ -818,13 +808,13 @@ struct ReduceSmem {
 // left out); each warp then walks a contiguous stretch of the concatenated
 // runs 32 entries per step, four steps of loads in flight.
 __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &p, const ReduceSmem &s, uint32_t b,
-                                              uint32_t accumulate, uint32_t *s_ok, uint32_t *s_warp,
-                                              uint32_t *status) {
+                                              uint32_t groups, uint32_t accumulate, uint32_t *s_ok,
+                                              uint64_t *s_warp, uint32_t *status) {
     const uint32_t G = p.g_cold, T = p.own_bins, tid = threadIdx.x, o = blockIdx.x;
     if (tid == 0) {
         bool ok = false;
         for (uint32_t k = 0; k < kSpinLimit; ++k)
-            if (ld_acquire(p.p1_done + b) >= G) {
+            if (ld_acquire(p.p1_done + b) >= G * groups) {
                 ok = true;
                 break;
             }
@@ -853,9 +843,11 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
             nonempty += len[v] ? 1u : 0u;
             mylen += len[v];
         }
-        uint32_t n_runs, total;
-        uint32_t pos = block_scan(nonempty, s_warp, &n_runs);
-        uint32_t epos = block_scan(mylen, s_warp, &total);
+        // one scan of both: runs in the high word, their entries in the low
+        uint64_t tot;
+        const uint64_t ex = block_scan64((uint64_t)nonempty << 32 | mylen, s_warp, &tot);
+        const uint32_t n_runs = (uint32_t)(tot >> 32), total = (uint32_t)tot;
+        uint32_t pos = (uint32_t)(ex >> 32), epos = (uint32_t)ex;
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
             if (!len[v]) continue;
@@ -938,53 +930,52 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
     return true;
 }
 
-// Both groups sort their share of bucket b's pages, then the bucket counts
-// this CTA as done.
+// Every group sorts its share of bucket b's pages; a CTA whose group ran out
+// of time stops with all its threads.
 template <int GROUPS>
 __device__ __forceinline__ bool sort_bucket(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t &seq,
                                             uint32_t *s_fail, uint32_t *status) {
     if (!sort_pages<GROUPS>(p, gs, b, seq, status)) *reinterpret_cast<volatile uint32_t *>(s_fail) = 1;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(p.p1_done + b, 1u);
-    }
     return *reinterpret_cast<volatile uint32_t *>(s_fail) == 0;
 }
 
 }  // namespace
 
-// Shared memory of the cold pass: GROUPS page-sorting groups, the run table,
-// the tile.
-__host__ __device__ constexpr size_t cold_group_bytes() { return 24ull * kPartPage; }
+// Shared memory of the cold pass: GROUPS page-sorting groups (two page
+// buffers and two owner-count arrays each), the run table, the tile.
+__host__ __device__ constexpr uint32_t cold_ocnt_words(uint32_t g_cold) { return (g_cold + 1 + 3) & ~3u; }
+__host__ __device__ constexpr size_t cold_group_bytes(uint32_t g_cold) {
+    return 16ull * kPartPage + 8ull * cold_ocnt_words(g_cold);
+}
 
 template <int GROUPS>
-__global__ void __launch_bounds__(GROUPS * 512, 1) k_part_cold(HistArgs h, PartDev p, uint32_t accumulate,
+__global__ void __launch_bounds__(kColdThreads, 1) k_part_cold(HistArgs h, PartDev p, uint32_t accumulate,
                                                                uint32_t *status) {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_gwarp[GROUPS][16];
-    __shared__ uint32_t s_ok, s_fail, s_gflag[GROUPS], s_id[GROUPS][2], s_fill[GROUPS][2];
+    __shared__ uint64_t s_warp[32];
+    __shared__ uint32_t s_ok, s_fail, s_gflag[GROUPS], s_id[GROUPS][2], s_fill[GROUPS][2], s_next[GROUPS];
     __shared__ uint64_t s_bar[GROUPS][2];
-    const uint32_t g = threadIdx.x / kGroupThreads;
-    const size_t ocnt_words = (p.g_cold + 1 + 3) & ~3u;
+    constexpr uint32_t GT = kColdThreads / GROUPS;
+    const uint32_t g = threadIdx.x / GT, ow = cold_ocnt_words(p.g_cold);
     GroupSmem gs;
-    uint8_t *gbase = smem + g * (cold_group_bytes() + 4 * ocnt_words);
+    uint8_t *gbase = smem + g * cold_group_bytes(p.g_cold);
     gs.buf[0] = reinterpret_cast<uint64_t *>(gbase);
     gs.buf[1] = gs.buf[0] + kPartPage;
-    gs.srt = gs.buf[1] + kPartPage;
-    gs.ocnt = reinterpret_cast<uint32_t *>(gs.srt + kPartPage);
+    gs.ocnt[0] = reinterpret_cast<uint32_t *>(gs.buf[1] + kPartPage);
+    gs.ocnt[1] = gs.ocnt[0] + ow;
     gs.bar = s_bar[g];
     gs.s_id = s_id[g];
     gs.s_fill = s_fill[g];
-    gs.s_warp = s_gwarp[g];
+    gs.s_next = &s_next[g];
     gs.s_flag = &s_gflag[g];
     gs.g = g;
     ReduceSmem rs;
-    rs.rpid = reinterpret_cast<uint32_t *>(smem + GROUPS * (cold_group_bytes() + 4 * ocnt_words));
+    rs.rpid = reinterpret_cast<uint32_t *>(smem + GROUPS * cold_group_bytes(p.g_cold));
     rs.rbeg = rs.rpid + kRunChunk;
     rs.rpre = rs.rbeg + kRunChunk;
     rs.tile = rs.rpre + kRunChunk + 4;
+    for (uint32_t i = threadIdx.x % GT; i < 2 * ow; i += GT) gs.ocnt[0][i] = 0;  // both arrays
     if (threadIdx.x == 0) {
         for (int k = 0; k < GROUPS; ++k) {
             mbar_init(smem_u32(&s_bar[k][0]), 1);
@@ -1000,7 +991,7 @@ __global__ void __launch_bounds__(GROUPS * 512, 1) k_part_cold(HistArgs h, PartD
     if (!sort_bucket<GROUPS>(p, gs, 0, seq, &s_fail, status)) return;
     for (uint32_t b = 0; b < p.n_buckets; ++b) {
         if (b + 1 < p.n_buckets && !sort_bucket<GROUPS>(p, gs, b + 1, seq, &s_fail, status)) return;
-        if (!reduce_bucket(h, p, rs, b, accumulate, &s_ok, s_warp, status)) return;
+        if (!reduce_bucket(h, p, rs, b, GROUPS, accumulate, &s_ok, s_warp, status)) return;
     }
 }
 
@@ -1057,11 +1048,14 @@ cudaError_t plan_partition(int lk, uint32_t table_smem, const RecArgs &r, const 
     const uint32_t nb = (uint32_t)(((uint64_t)h.n_bins + (1ull << cb) - 1) >> cb);
     const uint32_t T = (uint32_t)(((1ull << cb) + G - 1) / G);
     // two page-sorting groups where the tile leaves room, else one
-    const size_t group = cold_group_bytes() + 4ull * ((G + 1 + 3) & ~3u);
+    // four page-sorting groups where the tile leaves room, else two or one
+    // (1 KB for the kernel's static shared memory)
+    const size_t group = cold_group_bytes(G);
     const size_t tail = 12ull * kRunChunk + 16 + 24ull * T;
-    P.cold_groups = 2 * group + tail + 2048 <= smem_optin ? 2 : 1;
+    P.cold_groups = 4;
+    while (P.cold_groups > 1 && P.cold_groups * group + tail + 1024 > smem_optin) P.cold_groups /= 2;
     P.smem_cold = P.cold_groups * group + tail;
-    if (P.smem_cold + 2048 > smem_optin) return cudaErrorNotSupported;
+    if (P.smem_cold + 1024 > smem_optin) return cudaErrorNotSupported;
     // hot table: as many sets as shared memory allows (at least 2^4)
     const uint32_t tsm = (table_smem + 127u) & ~127u;
     uint32_t sb = 12;
@@ -1130,6 +1124,8 @@ cudaError_t plan_partition(int lk, uint32_t table_smem, const RecArgs &r, const 
     P.off_bucket_cnt = o;
     o = align256(o + 4ull * nb);
     P.off_p1_done = o;
+    o = align256(o + 4ull * nb);
+    P.off_pg_next = o;
     o = align256(o + 4ull * nb);
     P.off_hash_cnt = o;
     o = align256(o + (4ull << hb));
@@ -1202,6 +1198,7 @@ cudaError_t run_partition(int lk, const RecArgs &r, const TableArgs &t, const Hi
     d.page_list = reinterpret_cast<uint32_t *>(base + P.off_page_list);
     d.idx = reinterpret_cast<uint16_t *>(base + P.off_idx);
     d.p1_done = reinterpret_cast<uint32_t *>(base + P.off_p1_done);
+    d.pg_next = reinterpret_cast<uint32_t *>(base + P.off_pg_next);
     cudaError_t e;
     if ((e = cudaMemsetAsync(base + P.off_ff, 0xFF, P.bytes_ff, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(base + P.off_zero, 0, P.bytes_zero, c.stream)) != cudaSuccess) return e;
@@ -1222,15 +1219,13 @@ cudaError_t run_partition(int lk, const RecArgs &r, const TableArgs &t, const Hi
     HistArgs hh = h;
     uint32_t *status = c.status;
     void *args[] = {&hh, &d, &acc, &status};
-    if (P.cold_groups == 2) {
-        if ((e = set_smem(k_part_cold<2>, P.smem_cold)) != cudaSuccess) return e;
-        e = cudaLaunchCooperativeKernel((const void *)k_part_cold<2>, dim3(P.grid_cold), dim3(1024), args,
-                                        P.smem_cold, c.stream);
-    } else {
-        if ((e = set_smem(k_part_cold<1>, P.smem_cold)) != cudaSuccess) return e;
-        e = cudaLaunchCooperativeKernel((const void *)k_part_cold<1>, dim3(P.grid_cold), dim3(512), args,
-                                        P.smem_cold, c.stream);
-    }
+    const void *cold = P.cold_groups == 4   ? (const void *)k_part_cold<4>
+                       : P.cold_groups == 2 ? (const void *)k_part_cold<2>
+                                            : (const void *)k_part_cold<1>;
+    if ((e = cudaFuncSetAttribute(cold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem_cold)) !=
+        cudaSuccess)
+        return e;
+    e = cudaLaunchCooperativeKernel(cold, dim3(P.grid_cold), dim3(kColdThreads), args, P.smem_cold, c.stream);
     if (e != cudaSuccess) return e;
     k_part_hot_add<<<std::max<uint32_t>(1, P.slots / 256), 256, 0, c.stream>>>(h, P.d, P.slots);
     return cudaGetLastError();

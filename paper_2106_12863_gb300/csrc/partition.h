@@ -13,10 +13,11 @@
 //      (bin << 1 | direction, bytes) appended to a CTA-private page of its
 //      coarse bin range (a bucket);
 //   4. pages are grouped by bucket;
-//   5. cold pass (one cooperative launch): for each bucket in turn, every CTA
-//      sorts some of the bucket's pages by owner CTA in place (the pages stay
-//      in L2), then each CTA sums its own slice of the bucket's bins in a
-//      shared-memory tile and stores every bin of the slice once;
+//   5. cold pass (one cooperative launch): for each bucket in turn, the
+//      CTAs' page-sorting groups take the bucket's pages one at a time and
+//      sort each by owner CTA in place (the pages stay in L2), then each CTA
+//      sums its own slice of the bucket's bins in a shared-memory tile and
+//      stores every bin of the slice once;
 //   6. the hot table's totals are added to their bins.
 // Every update is counted exactly once: in a hot slot or as a cold entry.
 #pragma once
@@ -69,7 +70,8 @@ struct PartDev {
     uint32_t *bucket_pg;    // [n_buckets + 1] first position of each bucket in page_list
     uint32_t *page_list;    // [pages_cap] page ids, grouped by bucket
     uint16_t *idx;          // [pages_cap][g_cold + 1] owner run offsets of each sorted page
-    uint32_t *p1_done;      // [n_buckets] CTAs done sorting the bucket's pages
+    uint32_t *p1_done;      // [n_buckets] page-sorting groups done with the bucket
+    uint32_t *pg_next;      // [n_buckets] pages of the bucket handed out for sorting
     // cold pass geometry
     uint32_t g_cold;        // CTAs of the cold pass (= owners per bucket)
     uint32_t own_bins;      // bins per owner
@@ -87,14 +89,14 @@ struct PartPlan {
     PartDev d;                 // pointers filled once the scratch exists
     uint32_t slots;            // 4 << set_bits
     int grid_main, grid_sample, grid_cold;
-    int cold_groups;           // page-sorting groups of 512 threads in a cold-pass CTA (1 or 2)
+    int cold_groups;           // page-sorting groups in a 1,024-thread cold-pass CTA (1, 2 or 4)
     size_t smem_main, smem_sample, smem_cold;
     size_t scratch_bytes;
     // scratch layout (byte offsets)
     size_t off_ff, bytes_ff;   // region set to 0xFF (hash keys, hot keys)
     size_t off_zero, bytes_zero;  // region set to zero
     size_t off_hash_keys, off_hot_keys, off_levels, off_cand_n, off_page_alloc, off_hot_cnt,
-        off_hot_bytes, off_bucket_cnt, off_p1_done, off_hash_cnt, off_cand, off_page_bucket,
+        off_hot_bytes, off_bucket_cnt, off_p1_done, off_pg_next, off_hash_cnt, off_cand, off_page_bucket,
         off_page_fill, off_bucket_pg, off_page_list, off_idx, off_pages;
 };
 
