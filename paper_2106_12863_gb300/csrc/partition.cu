@@ -634,7 +634,6 @@ __global__ void __launch_bounds__(256) k_part_list_pages(PartDev p) {
 
 namespace {
 
-constexpr uint32_t kRunChunk = 1024;     // pages whose runs one staging of the run table covers
 constexpr uint32_t kColdThreads = 1024;  // threads of a cold-pass CTA (GROUPS page-sorting groups)
 
 // One page-sorting group's shared state: two page buffers (the copy of the
@@ -654,27 +653,6 @@ struct GroupSmem {
 template <int GROUPS>
 __device__ __forceinline__ void group_sync(uint32_t g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kColdThreads / GROUPS) : "memory");
-}
-
-// Block-wide exclusive scan of v (one value per thread of the whole CTA).
-__device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t *s_warp, uint64_t *total) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint64_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-    }
-    __syncthreads();
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    uint64_t woff = 0, t = 0;
-    for (uint32_t w = 0; w < nw; ++w) {
-        if (w < warp) woff += s_warp[w];
-        t += s_warp[w];
-    }
-    *total = t;
-    return woff + incl - v;
 }
 
 // The group's thread 0: start the TMA copy of the page at list position j into buf[k].
@@ -796,20 +774,17 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
     return true;
 }
 
-struct ReduceSmem {
-    uint32_t *rpid;  // [kRunChunk] run table: page id,
-    uint32_t *rbeg;  //   first entry of this owner's run in the page,
-    uint32_t *rpre;  //   [kRunChunk + 1] prefix of the runs' lengths
-    uint32_t *tile;  // [6][own_bins]: counts d0, d1; byte sums low d0, d1; high d0, d1
-};
-
 // Sum this CTA's bins of bucket b from every page's run, then store them.
-// The runs are staged in shared memory kRunChunk pages at a time (empty runs
-// left out); each warp then walks a contiguous stretch of the concatenated
-// runs 32 entries per step, four steps of loads in flight.
-__device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &p, const ReduceSmem &s, uint32_t b,
+// `tile` holds [6][own_bins] words: counts of directions 0 and 1, byte sums'
+// low words of both, high words of both. Each warp takes a contiguous share
+// of the bucket's pages, 32 at a time (one per lane): it reads their run
+// bounds, scans the run lengths across the warp, and walks the concatenated
+// runs 32 entries per step, four steps of loads in flight; a lane finds the
+// run of its entry by binary search over the warp's run starts (the last run
+// starting at or before the entry holds it, empty runs included).
+__device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &p, uint32_t *tile, uint32_t b,
                                               uint32_t groups, uint32_t accumulate, uint32_t *s_ok,
-                                              uint64_t *s_warp, uint32_t *status) {
+                                              uint32_t *status) {
     const uint32_t G = p.g_cold, T = p.own_bins, tid = threadIdx.x, o = blockIdx.x;
     if (tid == 0) {
         bool ok = false;
@@ -821,88 +796,55 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
         if (!ok) latch_status(status, SINET_ERR_TIMEOUT);
         *s_ok = ok ? 1u : 0u;
     }
-    for (uint32_t i = tid; i < 6 * T; i += blockDim.x) s.tile[i] = 0;
+    for (uint32_t i = tid; i < 6 * T; i += blockDim.x) tile[i] = 0;
     __syncthreads();
     if (!*s_ok) return false;
     const uint64_t lo_bin = ((uint64_t)b << p.cb_shift) + (uint64_t)o * T;
     const uint32_t warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-    for (uint32_t c0 = p.bucket_pg[b]; c0 < p.bucket_pg[b + 1]; c0 += kRunChunk) {
-        const uint32_t cn = min(kRunChunk, p.bucket_pg[b + 1] - c0);
-        // stage the non-empty runs (one or two pages per thread)
-        uint32_t id[2] = {0, 0}, e0[2] = {0, 0}, len[2] = {0, 0}, nonempty = 0, mylen = 0;
-        const uint32_t per = (kRunChunk + blockDim.x - 1) / blockDim.x;  // pages per thread: 1 or 2
+    const uint32_t pb = p.bucket_pg[b], pn = p.bucket_pg[b + 1] - pb;
+    const uint32_t w1 = pb + (uint32_t)((uint64_t)pn * (warp + 1) / nw);
+    for (uint32_t j0 = pb + (uint32_t)((uint64_t)pn * warp / nw); j0 < w1; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint32_t len = 0;
+        uint64_t at = 0;  // position in `pages` of the run's first entry
+        if (j < w1) {
+            const uint16_t *row = p.idx + (uint64_t)j * (G + 1);
+            const uint32_t e0 = row[o];
+            len = row[o + 1] - e0;
+            at = (uint64_t)p.page_list[j] * kPartPage + e0;
+        }
+        uint32_t incl = len;
 #pragma unroll
-        for (int v = 0; v < 2; ++v) {
-            const uint32_t i = tid * per + (uint32_t)v;
-            if ((uint32_t)v < per && i < cn) {
-                const uint16_t *row = p.idx + (uint64_t)(c0 + i) * (G + 1);
-                e0[v] = row[o];
-                len[v] = row[o + 1] - e0[v];
-                if (len[v]) id[v] = p.page_list[c0 + i];
-            }
-            nonempty += len[v] ? 1u : 0u;
-            mylen += len[v];
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
         }
-        // one scan of both: runs in the high word, their entries in the low
-        uint64_t tot;
-        const uint64_t ex = block_scan64((uint64_t)nonempty << 32 | mylen, s_warp, &tot);
-        const uint32_t n_runs = (uint32_t)(tot >> 32), total = (uint32_t)tot;
-        uint32_t pos = (uint32_t)(ex >> 32), epos = (uint32_t)ex;
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-            if (!len[v]) continue;
-            s.rpid[pos] = id[v];
-            s.rbeg[pos] = e0[v];
-            s.rpre[pos] = epos;
-            ++pos;
-            epos += len[v];
-        }
-        if (tid == 0) s.rpre[n_runs] = total;
-        __syncthreads();
-        // this warp's stretch of the runs' entries
-        const uint32_t span = ((total + nw - 1) / nw + 31) & ~31u;
-        const uint32_t k0 = min(total, warp * span), k1 = min(total, k0 + span);
-        uint32_t r = 0;
-        if (k0 < k1) {  // first run holding entry k0: the last with rpre <= k0
-            uint32_t lo = 0, n = n_runs;
-            while (n > 1) {
-                const uint32_t half = n >> 1;
-                if (s.rpre[lo + half] <= k0) lo += half;
-                n -= half;
-            }
-            r = lo;
-        }
-        for (uint32_t base = k0; base < k1; base += 4 * 32) {
+        const uint32_t start = incl - len, total = __shfl_sync(kFull, incl, 31);
+        for (uint32_t k0 = 0; k0 < total; k0 += 4 * 32) {
             uint64_t e[4];
-            uint32_t ok_mask = 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const uint32_t k = base + (uint32_t)u * 32 + lane;
-                uint32_t my = kNoKey;
-                for (;;) {  // warp-uniform: advance r until every live lane has its run
-                    const uint32_t end = s.rpre[r + 1];
-                    if (my == kNoKey && k < end) my = r;
-                    if (!__any_sync(kFull, my == kNoKey && k < k1)) break;
-                    ++r;
-                }
-                e[u] = 0;
-                if (k < k1) {
-                    e[u] = p.pages[(uint64_t)s.rpid[my] * kPartPage + s.rbeg[my] + (k - s.rpre[my])];
-                    ok_mask |= 1u << u;
-                }
+                const uint32_t k = k0 + (uint32_t)u * 32 + lane;
+                uint32_t r = 0;
+#pragma unroll
+                for (uint32_t s = 16; s; s >>= 1)
+                    if (__shfl_sync(kFull, start, (int)(r + s)) <= k) r += s;
+                const uint64_t a = __shfl_sync(kFull, at, (int)r);
+                const uint32_t sr = __shfl_sync(kFull, start, (int)r);
+                e[u] = k < total ? p.pages[a + (k - sr)] : 0ull;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (!(ok_mask >> u & 1u)) continue;
+                if (k0 + (uint32_t)u * 32 + lane >= total) continue;
                 const uint32_t key = (uint32_t)(e[u] >> 32);
                 const uint32_t d = key & 1u;
                 const uint32_t tb = (uint32_t)((key >> 1) - lo_bin);
-                atomicAdd(s.tile + d * T + tb, 1u);
-                smem_add_wide(s.tile + (2 + d) * T + tb, s.tile + (4 + d) * T + tb, (uint32_t)e[u], 0u);
+                atomicAdd(tile + d * T + tb, 1u);
+                smem_add_wide(tile + (2 + d) * T + tb, tile + (4 + d) * T + tb, (uint32_t)e[u], 0u);
             }
         }
-        __syncthreads();  // before the next chunk's run table
     }
+    __syncthreads();
     uint64_t hi_bin = lo_bin + T;
     const uint64_t b_end = (uint64_t)(b + 1) << p.cb_shift;
     if (hi_bin > b_end) hi_bin = b_end;
@@ -911,9 +853,9 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
         const uint32_t n = (uint32_t)(hi_bin - lo_bin);
         for (uint32_t i = tid; i < n; i += blockDim.x) {
             const uint64_t bin = lo_bin + i;
-            uint32_t c0 = s.tile[i], c1 = s.tile[T + i];
-            uint64_t s0 = (uint64_t)s.tile[4 * T + i] << 32 | s.tile[2 * T + i];
-            uint64_t s1 = (uint64_t)s.tile[5 * T + i] << 32 | s.tile[3 * T + i];
+            uint32_t c0 = tile[i], c1 = tile[T + i];
+            uint64_t s0 = (uint64_t)tile[4 * T + i] << 32 | tile[2 * T + i];
+            uint64_t s1 = (uint64_t)tile[5 * T + i] << 32 | tile[3 * T + i];
             if (accumulate) {
                 c0 += h.cnt[0][bin];
                 c1 += h.cnt[1][bin];
@@ -943,7 +885,7 @@ __device__ __forceinline__ bool sort_bucket(const PartDev &p, const GroupSmem &g
 }  // namespace
 
 // Shared memory of the cold pass: GROUPS page-sorting groups (two page
-// buffers and two owner-count arrays each), the run table, the tile.
+// buffers and two owner-count arrays each), then the tile.
 __host__ __device__ constexpr uint32_t cold_ocnt_words(uint32_t g_cold) { return (g_cold + 1 + 3) & ~3u; }
 __host__ __device__ constexpr size_t cold_group_bytes(uint32_t g_cold) {
     return 16ull * kPartPage + 8ull * cold_ocnt_words(g_cold);
@@ -953,7 +895,6 @@ template <int GROUPS>
 __global__ void __launch_bounds__(kColdThreads, 1) k_part_cold(HistArgs h, PartDev p, uint32_t accumulate,
                                                                uint32_t *status) {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint64_t s_warp[32];
     __shared__ uint32_t s_ok, s_fail, s_gflag[GROUPS], s_id[GROUPS][2], s_fill[GROUPS][2], s_next[GROUPS];
     __shared__ uint64_t s_bar[GROUPS][2];
     constexpr uint32_t GT = kColdThreads / GROUPS;
@@ -970,11 +911,7 @@ __global__ void __launch_bounds__(kColdThreads, 1) k_part_cold(HistArgs h, PartD
     gs.s_next = &s_next[g];
     gs.s_flag = &s_gflag[g];
     gs.g = g;
-    ReduceSmem rs;
-    rs.rpid = reinterpret_cast<uint32_t *>(smem + GROUPS * cold_group_bytes(p.g_cold));
-    rs.rbeg = rs.rpid + kRunChunk;
-    rs.rpre = rs.rbeg + kRunChunk;
-    rs.tile = rs.rpre + kRunChunk + 4;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem + GROUPS * cold_group_bytes(p.g_cold));
     for (uint32_t i = threadIdx.x % GT; i < 2 * ow; i += GT) gs.ocnt[0][i] = 0;  // both arrays
     if (threadIdx.x == 0) {
         for (int k = 0; k < GROUPS; ++k) {
@@ -991,7 +928,7 @@ __global__ void __launch_bounds__(kColdThreads, 1) k_part_cold(HistArgs h, PartD
     if (!sort_bucket<GROUPS>(p, gs, 0, seq, &s_fail, status)) return;
     for (uint32_t b = 0; b < p.n_buckets; ++b) {
         if (b + 1 < p.n_buckets && !sort_bucket<GROUPS>(p, gs, b + 1, seq, &s_fail, status)) return;
-        if (!reduce_bucket(h, p, rs, b, GROUPS, accumulate, &s_ok, s_warp, status)) return;
+        if (!reduce_bucket(h, p, tile, b, GROUPS, accumulate, &s_ok, status)) return;
     }
 }
 
@@ -1051,7 +988,7 @@ cudaError_t plan_partition(int lk, uint32_t table_smem, const RecArgs &r, const 
     // four page-sorting groups where the tile leaves room, else two or one
     // (1 KB for the kernel's static shared memory)
     const size_t group = cold_group_bytes(G);
-    const size_t tail = 12ull * kRunChunk + 16 + 24ull * T;
+    const size_t tail = 24ull * T;
     P.cold_groups = 4;
     while (P.cold_groups > 1 && P.cold_groups * group + tail + 1024 > smem_optin) P.cold_groups /= 2;
     P.smem_cold = P.cold_groups * group + tail;
