@@ -241,46 +241,62 @@ struct MainSmem {
     uint32_t *hcnt;         // [2][slots]
     uint32_t *hlo;          // [2][slots] byte sums, low words
     uint32_t *hhi;          // [2][slots] byte sums, high words
-    uint64_t *slot;         // [n_buckets][4] page index << 32 | page id of the last four pages
+    uint64_t *slot;         // [n_buckets][4] page index << 32 | page id of the last four overflow pages
     uint32_t *cur;          // [n_buckets] cold entries appended so far
     uint32_t slots;
     uint32_t shift;         // 32 - set_bits
+    uint32_t rbase;         // first page of this CTA's region: blockIdx.x * n_buckets * creg
+    uint32_t quiet;         // positions below this need no overflow page: creg * kPartPage - kPartPage / 2
 };
+
+// Page k of bucket bk's overflow, taken from the pool's shared part (page
+// ids from dyn_base on), into its slot.
+__device__ __forceinline__ void alloc_overflow(const PartDev &p, const MainSmem &m, uint32_t bk, uint32_t k,
+                                            uint32_t *status) {
+    const uint32_t nxt = p.dyn_base + atomicAdd(p.page_alloc, 1u);
+    if (nxt < p.pages_cap) {
+        p.page_bucket[nxt] = bk;
+        p.page_fill[nxt] = kPartPage;
+    } else {
+        latch_status(status, SINET_ERR_BUDGET);
+    }
+    reinterpret_cast<volatile uint64_t *>(m.slot)[4 * bk + (k & 3)] = (uint64_t)k << 32 | nxt;
+}
 
 // Append one cold entry (key = bin << 1 | direction, the record's bytes) to
 // the CTA's current page of the bin's bucket. Positions come from a
-// shared-memory counter; the thread that takes the middle position of a page
-// allocates the next page, so the page a position falls in is (almost)
-// always ready. Four slots per bucket keep (page index, page id) of the
-// current pages in one 64-bit word each, written and read whole, so no fence
-// is needed: a thread holds at most one claimed position at a time, so the
-// claimed but unwritten positions (at most one per thread) stay within two
-// pages and a slot is never reused while a thread still needs it.
+// shared-memory counter. Pages 0 .. creg - 1 of every bucket are the CTA's
+// own region of the pool, their ids fixed by CTA, bucket and page index.
+// Later pages (overflow) come from the pool's shared part: the thread that
+// takes the middle position of page k - 1 allocates page k, so the page a
+// position falls in is (almost) always ready. Four slots per bucket keep
+// (page index, page id) of the current overflow pages in one 64-bit word
+// each, written and read whole, so no fence is needed: a thread holds at most
+// one claimed position at a time, so the claimed but unwritten positions (at
+// most one per thread) stay within two pages and a slot is never reused while
+// a thread still needs it.
 __device__ __forceinline__ void cold_emit_entry(const PartDev &p, const MainSmem &m, uint64_t e, uint32_t *status) {
     const uint32_t bk = (uint32_t)(e >> 33) >> p.cb_shift;
     const uint32_t pos = atomicAdd(m.cur + bk, 1u);
     const uint32_t pg = pos >> kPartPageBits, off = pos & (kPartPage - 1);
-    volatile uint64_t *sl = m.slot + 4 * bk;
-    if (off == kPartPage / 2) {
-        const uint32_t nxt = atomicAdd(p.page_alloc, 1u);
-        if (nxt < p.pages_cap) {
-            p.page_bucket[nxt] = bk;
-            p.page_fill[nxt] = kPartPage;
-        } else {
-            latch_status(status, SINET_ERR_BUDGET);
+    uint32_t id = m.rbase + bk * p.creg + pg;
+    if (pos >= m.quiet) {  // from the middle of the region's last page on
+        if (off == kPartPage / 2) alloc_overflow(p, m, bk, pg + 1, status);
+        if (pg >= p.creg) {
+            volatile uint64_t *sl = m.slot + 4 * bk;
+            uint64_t v = sl[pg & 3];
+            for (uint32_t k = 0; (uint32_t)(v >> 32) != pg; ++k) {
+                if (k > kSpinLimit) {
+                    latch_status(status, SINET_ERR_TIMEOUT);
+                    return;
+                }
+                v = sl[pg & 3];
+            }
+            id = (uint32_t)v;
+            if (id >= p.pages_cap) return;
         }
-        sl[(pg + 1) & 3] = (uint64_t)(pg + 1) << 32 | nxt;
     }
-    uint64_t v = sl[pg & 3];
-    for (uint32_t k = 0; (uint32_t)(v >> 32) != pg; ++k) {
-        if (k > kSpinLimit) {
-            latch_status(status, SINET_ERR_TIMEOUT);
-            return;
-        }
-        v = sl[pg & 3];
-    }
-    const uint32_t id = (uint32_t)v;
-    if (id < p.pages_cap) p.pages[(uint64_t)id * kPartPage + off] = e;
+    p.pages[(uint64_t)id * kPartPage + off] = e;
 }
 
 __device__ __forceinline__ void cold_emit(const PartDev &p, const MainSmem &m, uint32_t key, uint32_t by,
@@ -389,6 +405,8 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
     MainSmem m;
     m.slots = 4u << p.set_bits;
     m.shift = 32 - p.set_bits;
+    m.rbase = blockIdx.x * p.n_buckets * p.creg;
+    m.quiet = p.creg * kPartPage - kPartPage / 2;
     uint32_t *hk = reinterpret_cast<uint32_t *>(stage + kPartStages * kPartStageBytes);
     m.hkeys = hk;
     m.hcnt = hk + m.slots;
@@ -403,18 +421,9 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
         m.hlo[i] = 0;
         m.hhi[i] = 0;
     }
-    // page 0 of every bucket up front
     for (uint32_t b = tid; b < p.n_buckets; b += blockDim.x) {
         m.cur[b] = 0;
-        const uint32_t id = atomicAdd(p.page_alloc, 1u);
-        if (id < p.pages_cap) {
-            p.page_bucket[id] = b;
-            p.page_fill[id] = kPartPage;
-        } else {
-            latch_status(status, SINET_ERR_BUDGET);
-        }
-        m.slot[4 * b] = id;  // page 0
-        m.slot[4 * b + 1] = m.slot[4 * b + 2] = m.slot[4 * b + 3] = ~0ull;
+        m.slot[4 * b] = m.slot[4 * b + 1] = m.slot[4 * b + 2] = m.slot[4 * b + 3] = ~0ull;
     }
     if (tid < 6) s_cnt[tid] = 0;
     if (tid == 0) {
@@ -571,11 +580,19 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
             }
         }
     }
-    // fills of each bucket's last two pages (every earlier page is full)
+    // fills: every page of the region, then each bucket's last two overflow
+    // pages (every earlier overflow page is full)
+    for (uint32_t i = tid; i < p.n_buckets * p.creg; i += blockDim.x) {
+        const uint32_t b = i / p.creg, k = i - b * p.creg;
+        const int64_t f = (int64_t)m.cur[b] - (int64_t)k * kPartPage;
+        p.page_bucket[m.rbase + i] = b;
+        p.page_fill[m.rbase + i] = (uint32_t)(f < 0 ? 0 : f > kPartPage ? kPartPage : f);
+    }
     for (uint32_t b = tid; b < p.n_buckets; b += blockDim.x) {
         const uint32_t E = m.cur[b];
         const uint32_t ka = E > kPartPage / 2 ? ((E - kPartPage / 2 - 1) >> kPartPageBits) + 1 : 0u;
         for (uint32_t k = ka ? ka - 1 : 0; k <= ka; ++k) {
+            if (k < p.creg) continue;
             const uint64_t v = m.slot[4 * b + (k & 3)];
             if ((uint32_t)(v >> 32) != k) continue;
             const uint32_t id = (uint32_t)v;
@@ -586,14 +603,20 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
 }
 
 // ---------------------------------------------------------------------------
-// 4. Pages grouped by bucket: counts, their scan, the lists.
+// 4. Pages grouped by bucket: counts, their scan, the lists. A page is
+// listed when it holds entries (a region page a CTA left unused has fill 0).
+__device__ __forceinline__ bool page_listed(const PartDev &p, uint32_t id) {
+    const uint32_t f = p.page_fill[id];
+    return f != 0 && f <= kPartPage && p.page_bucket[id] < p.n_buckets;
+}
+
 __global__ void __launch_bounds__(256) k_part_count_pages(PartDev p) {
     __shared__ uint32_t s[kPartMaxBuckets];
     for (uint32_t i = threadIdx.x; i < p.n_buckets; i += blockDim.x) s[i] = 0;
     __syncthreads();
-    const uint32_t n = min(*p.page_alloc, p.pages_cap);
+    const uint32_t n = (uint32_t)min((uint64_t)p.dyn_base + *p.page_alloc, (uint64_t)p.pages_cap);
     for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x)
-        if (p.page_fill[id]) atomicAdd(&s[p.page_bucket[id]], 1u);
+        if (page_listed(p, id)) atomicAdd(&s[p.page_bucket[id]], 1u);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < p.n_buckets; i += blockDim.x)
         if (s[i]) atomicAdd(p.bucket_cnt + i, s[i]);
@@ -615,9 +638,9 @@ __global__ void __launch_bounds__(kPartMaxBuckets) k_part_scan_pages(PartDev p) 
 }
 
 __global__ void __launch_bounds__(256) k_part_list_pages(PartDev p) {
-    const uint32_t n = min(*p.page_alloc, p.pages_cap);
+    const uint32_t n = (uint32_t)min((uint64_t)p.dyn_base + *p.page_alloc, (uint64_t)p.pages_cap);
     for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
-        if (!p.page_fill[id]) continue;
+        if (!page_listed(p, id)) continue;
         const uint32_t b = p.page_bucket[id];
         const uint32_t pos = atomicAdd(p.bucket_cnt + b, 1u);
         p.page_list[p.bucket_pg[b] + pos] = id;
@@ -839,6 +862,10 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
                 const uint32_t key = (uint32_t)(e[u] >> 32);
                 const uint32_t d = key & 1u;
                 const uint32_t tb = (uint32_t)((key >> 1) - lo_bin);
+                if (tb >= T) {  // not this owner's bin: cannot happen for a sorted page
+                    latch_status(status, SINET_ERR_DEVICE_CHECK);
+                    continue;
+                }
                 atomicAdd(tile + d * T + tb, 1u);
                 smem_add_wide(tile + (2 + d) * T + tb, tile + (4 + d) * T + tb, (uint32_t)e[u], 0u);
             }
@@ -1032,8 +1059,15 @@ cudaError_t plan_partition(int lk, uint32_t table_smem, const RecArgs &r, const 
     d.hash_shift = 32 - hb;
     d.sample_chunks = s_chunks;
     d.sample_stride = stride;
-    const uint64_t cap = (routed_max + kPartPage - 1) / kPartPage + 2ull * G * nb + 1;
+    // pages: each CTA's region of creg pages per bucket (room for a cold
+    // share of 30 % of the routed updates, spread evenly, plus one page),
+    // then the shared part, which alone holds every routed update
+    const uint64_t per_region = (3 * routed_max / 10 + (uint64_t)G * nb * kPartPage - 1) / ((uint64_t)G * nb * kPartPage);
+    d.creg = (uint32_t)std::min<uint64_t>(16, per_region + 1);
+    const uint64_t regions = (uint64_t)G * nb * d.creg;
+    const uint64_t cap = regions + (routed_max + kPartPage - 1) / kPartPage + 2ull * G * nb + 1;
     if (cap >= 0xFFFFFFFFull) return cudaErrorNotSupported;
+    d.dyn_base = (uint32_t)regions;
     d.pages_cap = (uint32_t)cap;
     P.grid_main = G;
     P.grid_sample = G;
@@ -1139,6 +1173,8 @@ cudaError_t run_partition(int lk, const RecArgs &r, const TableArgs &t, const Hi
     cudaError_t e;
     if ((e = cudaMemsetAsync(base + P.off_ff, 0xFF, P.bytes_ff, c.stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(base + P.off_zero, 0, P.bytes_zero, c.stream)) != cudaSuccess) return e;
+    // region pages count as empty unless their CTA records a fill
+    if ((e = cudaMemsetAsync(d.page_fill, 0, 4ull * d.dyn_base, c.stream)) != cudaSuccess) return e;
     switch (lk) {
         case LK_INTERVAL: e = launch_lk<LK_INTERVAL>(r, t, h, P, c); break;
         case LK_TOGGLE1: e = launch_lk<LK_TOGGLE1>(r, t, h, P, c); break;

@@ -57,8 +57,12 @@ struct PartDev {
     uint32_t *hot_cnt;    // [2][slots]
     uint64_t *hot_bytes;  // [2][slots]
     uint32_t set_bits;
-    // cold entries: pages of kPartPage u64 entries, one bucket each
-    uint32_t *page_alloc;   // pages handed out
+    // cold entries: pages of kPartPage u64 entries, one bucket each. Pages
+    // [0, dyn_base) are the CTAs' regions (CTA c's page k of bucket b is
+    // (c * n_buckets + b) * creg + k); later pages are handed out on demand.
+    uint32_t creg;          // region pages per CTA and bucket (at least 1)
+    uint32_t dyn_base;      // first page handed out on demand
+    uint32_t *page_alloc;   // pages handed out on demand
     uint32_t *page_bucket;  // [pages_cap]
     uint32_t *page_fill;    // [pages_cap] entries in the page
     uint64_t *pages;        // [pages_cap][kPartPage]
