@@ -657,7 +657,10 @@ __global__ void __launch_bounds__(256) k_part_list_pages(PartDev p) {
 
 namespace {
 
-constexpr uint32_t kColdThreads = 1024;  // threads of a cold-pass CTA (GROUPS page-sorting groups)
+constexpr uint32_t kColdThreads = 1024;  // threads of a cold-pass CTA: SG sorting groups, then reducers
+constexpr uint32_t kSortThreads = 256;   // threads of one page-sorting group
+constexpr uint32_t kReduceBar = 15;      // named barrier of the reducing warps
+constexpr uint32_t kSortAhead = 8;       // buckets the sorting groups may run ahead of the reducers
 
 // One page-sorting group's shared state: two page buffers (the copy of the
 // next page lands in one while the page in the other is sorted in place) and
@@ -673,9 +676,13 @@ struct GroupSmem {
     uint32_t g;         // group index (named barrier 1 + g)
 };
 
-template <int GROUPS>
 __device__ __forceinline__ void group_sync(uint32_t g) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kColdThreads / GROUPS) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kSortThreads) : "memory");
+}
+
+template <uint32_t NR>
+__device__ __forceinline__ void reduce_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kReduceBar), "n"(NR) : "memory");
 }
 
 // The group's thread 0: start the TMA copy of the page at list position j into buf[k].
@@ -707,21 +714,20 @@ __device__ __forceinline__ uint32_t claim_page(const PartDev &p, const GroupSmem
 // page, into the other buffer, starts after the first). `seq` counts the
 // group's pages over all buckets (buffer and phase). Returns false when a
 // page copy's wait ran out.
-template <int GROUPS>
 __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t &seq,
                                            uint32_t *status) {
-    constexpr uint32_t GT = kColdThreads / GROUPS;
+    constexpr uint32_t GT = kSortThreads;
     constexpr int U = kPartPage / GT;
     const uint32_t G = p.g_cold, tid = threadIdx.x % GT, lane = tid & 31;
     const uint32_t bmask = (1u << p.cb_shift) - 1u, end = p.bucket_pg[b + 1];
     volatile uint32_t *s_next = gs.s_next;
     if (tid == 0) *s_next = claim_page(p, gs, b, seq & 1u);
-    group_sync<GROUPS>(gs.g);
+    group_sync(gs.g);
     for (uint32_t j = *s_next; j < end; ++seq) {
         const uint32_t k = seq & 1u;
         // bounded wait for this page's copy (phase = uses of buffer k so far)
         if (!mbar_wait(smem_u32(gs.bar + k), (seq >> 1) & 1u)) *reinterpret_cast<volatile uint32_t *>(gs.s_flag) = 1;
-        group_sync<GROUPS>(gs.g);
+        group_sync(gs.g);
         if (*reinterpret_cast<volatile uint32_t *>(gs.s_flag)) {
             if (tid == 0) latch_status(status, SINET_ERR_TIMEOUT);
             return false;
@@ -748,7 +754,7 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
         // them wrote its row before the barrier above)
         uint32_t *on = gs.ocnt[k ^ 1u];
         for (uint32_t o = tid; o <= G; o += GT) on[o] = 0;
-        group_sync<GROUPS>(gs.g);
+        group_sync(gs.g);
         // exclusive scan of the G + 1 counts by the group's first warp (the
         // last count is always zero, so its offset is the page's fill)
         if (tid < 32) {
@@ -770,14 +776,14 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
                 ex += c;
             }
         }
-        group_sync<GROUPS>(gs.g);
+        group_sync(gs.g);
         // every entry is in registers: scatter them in place, owner by owner
 #pragma unroll
         for (int u = 0; u < U; ++u)
             if (tid + (uint32_t)u * GT < fill) pg[oc[pos[u] >> 16] + (pos[u] & 0xFFFFu)] = ent[u];
         uint16_t *row = p.idx + (uint64_t)j * (G + 1);
         for (uint32_t o = tid; o <= G; o += GT) row[o] = (uint16_t)oc[o];
-        group_sync<GROUPS>(gs.g);
+        group_sync(gs.g);
         // back to the page, 16 bytes per store
         uint4 *dst = reinterpret_cast<uint4 *>(p.pages + (uint64_t)id * kPartPage);
         const uint4 *v = reinterpret_cast<const uint4 *>(pg);
@@ -792,7 +798,7 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
     }
     // the group's pages and rows are stored: count the group done with bucket b
     __threadfence();
-    group_sync<GROUPS>(gs.g);
+    group_sync(gs.g);
     if (tid == 0) atomicAdd(p.p1_done + b, 1u);
     return true;
 }
@@ -805,25 +811,28 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
 // runs 32 entries per step, four steps of loads in flight; a lane finds the
 // run of its entry by binary search over the warp's run starts (the last run
 // starting at or before the entry holds it, empty runs included).
+template <uint32_t NR>
 __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &p, uint32_t *tile, uint32_t b,
                                               uint32_t groups, uint32_t accumulate, uint32_t *s_ok,
-                                              uint32_t *status) {
-    const uint32_t G = p.g_cold, T = p.own_bins, tid = threadIdx.x, o = blockIdx.x;
+                                              const uint32_t *s_fail, uint32_t tid, uint32_t *status) {
+    const uint32_t G = p.g_cold, T = p.own_bins, o = blockIdx.x;
     if (tid == 0) {
         bool ok = false;
-        for (uint32_t k = 0; k < kSpinLimit; ++k)
+        for (uint32_t k = 0; k < kSpinLimit; ++k) {
             if (ld_acquire(p.p1_done + b) >= G * groups) {
                 ok = true;
                 break;
             }
+            if (*reinterpret_cast<const volatile uint32_t *>(s_fail)) break;
+        }
         if (!ok) latch_status(status, SINET_ERR_TIMEOUT);
         *s_ok = ok ? 1u : 0u;
     }
-    for (uint32_t i = tid; i < 6 * T; i += blockDim.x) tile[i] = 0;
-    __syncthreads();
+    for (uint32_t i = tid; i < 6 * T; i += NR) tile[i] = 0;
+    reduce_sync<NR>();
     if (!*s_ok) return false;
     const uint64_t lo_bin = ((uint64_t)b << p.cb_shift) + (uint64_t)o * T;
-    const uint32_t warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    const uint32_t warp = tid >> 5, lane = tid & 31, nw = NR >> 5;
     const uint32_t pb = p.bucket_pg[b], pn = p.bucket_pg[b + 1] - pb;
     const uint32_t w1 = pb + (uint32_t)((uint64_t)pn * (warp + 1) / nw);
     for (uint32_t j0 = pb + (uint32_t)((uint64_t)pn * warp / nw); j0 < w1; j0 += 32) {
@@ -871,14 +880,14 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
             }
         }
     }
-    __syncthreads();
+    reduce_sync<NR>();
     uint64_t hi_bin = lo_bin + T;
     const uint64_t b_end = (uint64_t)(b + 1) << p.cb_shift;
     if (hi_bin > b_end) hi_bin = b_end;
     if (hi_bin > h.n_bins) hi_bin = h.n_bins;
     if (lo_bin < hi_bin) {
         const uint32_t n = (uint32_t)(hi_bin - lo_bin);
-        for (uint32_t i = tid; i < n; i += blockDim.x) {
+        for (uint32_t i = tid; i < n; i += NR) {
             const uint64_t bin = lo_bin + i;
             uint32_t c0 = tile[i], c1 = tile[T + i];
             uint64_t s0 = (uint64_t)tile[4 * T + i] << 32 | tile[2 * T + i];
@@ -895,68 +904,98 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
             h.byt[1][bin] = s1;
         }
     }
-    __syncthreads();
+    reduce_sync<NR>();  // the tile is zeroed for the next bucket after every store
     return true;
-}
-
-// Every group sorts its share of bucket b's pages; a CTA whose group ran out
-// of time stops with all its threads.
-template <int GROUPS>
-__device__ __forceinline__ bool sort_bucket(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t &seq,
-                                            uint32_t *s_fail, uint32_t *status) {
-    if (!sort_pages<GROUPS>(p, gs, b, seq, status)) *reinterpret_cast<volatile uint32_t *>(s_fail) = 1;
-    __syncthreads();
-    return *reinterpret_cast<volatile uint32_t *>(s_fail) == 0;
 }
 
 }  // namespace
 
-// Shared memory of the cold pass: GROUPS page-sorting groups (two page
-// buffers and two owner-count arrays each), then the tile.
+// Shared memory of the cold pass: SG page-sorting groups (two page buffers
+// and two owner-count arrays each), then the tile.
 __host__ __device__ constexpr uint32_t cold_ocnt_words(uint32_t g_cold) { return (g_cold + 1 + 3) & ~3u; }
 __host__ __device__ constexpr size_t cold_group_bytes(uint32_t g_cold) {
     return 16ull * kPartPage + 8ull * cold_ocnt_words(g_cold);
 }
 
-template <int GROUPS>
+// Threads [0, SG * 256) are SG page-sorting groups; they sort bucket after
+// bucket, at most kSortAhead buckets ahead of this CTA's reducers. The other
+// threads reduce: bucket after bucket, once every group of every CTA has
+// sorted it. The two roles meet only at those two waits, so the sorting's
+// barriers and the gathering's loads overlap. A role that fails (a bounded
+// wait ran out) sets s_fail and the other stops at its next bucket.
+template <int SG>
 __global__ void __launch_bounds__(kColdThreads, 1) k_part_cold(HistArgs h, PartDev p, uint32_t accumulate,
                                                                uint32_t *status) {
+    constexpr uint32_t NS = SG * kSortThreads, NR = kColdThreads - NS;
+    static_assert(SG >= 1 && NR >= 64, "room for the reducing warps");
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint32_t s_ok, s_fail, s_gflag[GROUPS], s_id[GROUPS][2], s_fill[GROUPS][2], s_next[GROUPS];
-    __shared__ uint64_t s_bar[GROUPS][2];
-    constexpr uint32_t GT = kColdThreads / GROUPS;
-    const uint32_t g = threadIdx.x / GT, ow = cold_ocnt_words(p.g_cold);
-    GroupSmem gs;
-    uint8_t *gbase = smem + g * cold_group_bytes(p.g_cold);
-    gs.buf[0] = reinterpret_cast<uint64_t *>(gbase);
-    gs.buf[1] = gs.buf[0] + kPartPage;
-    gs.ocnt[0] = reinterpret_cast<uint32_t *>(gs.buf[1] + kPartPage);
-    gs.ocnt[1] = gs.ocnt[0] + ow;
-    gs.bar = s_bar[g];
-    gs.s_id = s_id[g];
-    gs.s_fill = s_fill[g];
-    gs.s_next = &s_next[g];
-    gs.s_flag = &s_gflag[g];
-    gs.g = g;
-    uint32_t *tile = reinterpret_cast<uint32_t *>(smem + GROUPS * cold_group_bytes(p.g_cold));
-    for (uint32_t i = threadIdx.x % GT; i < 2 * ow; i += GT) gs.ocnt[0][i] = 0;  // both arrays
+    __shared__ uint32_t s_ok, s_fail, s_reduced, s_go[SG], s_gflag[SG], s_id[SG][2], s_fill[SG][2], s_next[SG];
+    __shared__ uint64_t s_bar[SG][2];
+    const uint32_t ow = cold_ocnt_words(p.g_cold);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem + SG * cold_group_bytes(p.g_cold));
+    if (threadIdx.x < NS) {  // both owner-count arrays of every group start at zero
+        uint32_t *oc = reinterpret_cast<uint32_t *>(smem + (threadIdx.x / kSortThreads) * cold_group_bytes(p.g_cold) +
+                                                    16ull * kPartPage);
+        for (uint32_t i = threadIdx.x % kSortThreads; i < 2 * ow; i += kSortThreads) oc[i] = 0;
+    }
     if (threadIdx.x == 0) {
-        for (int k = 0; k < GROUPS; ++k) {
+        for (int k = 0; k < SG; ++k) {
             mbar_init(smem_u32(&s_bar[k][0]), 1);
             mbar_init(smem_u32(&s_bar[k][1]), 1);
             s_gflag[k] = 0;
         }
         s_fail = 0;
+        s_reduced = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (p.n_buckets == 0) return;
-    uint32_t seq = 0;
-    if (!sort_bucket<GROUPS>(p, gs, 0, seq, &s_fail, status)) return;
-    for (uint32_t b = 0; b < p.n_buckets; ++b) {
-        if (b + 1 < p.n_buckets && !sort_bucket<GROUPS>(p, gs, b + 1, seq, &s_fail, status)) return;
-        if (!reduce_bucket(h, p, tile, b, GROUPS, accumulate, &s_ok, status)) return;
+    volatile uint32_t *fail = &s_fail, *reduced = &s_reduced;
+    if (threadIdx.x < NS) {
+        const uint32_t g = threadIdx.x / kSortThreads, t = threadIdx.x % kSortThreads;
+        GroupSmem gs;
+        gs.buf[0] = reinterpret_cast<uint64_t *>(smem + g * cold_group_bytes(p.g_cold));
+        gs.buf[1] = gs.buf[0] + kPartPage;
+        gs.ocnt[0] = reinterpret_cast<uint32_t *>(gs.buf[1] + kPartPage);
+        gs.ocnt[1] = gs.ocnt[0] + ow;
+        gs.bar = s_bar[g];
+        gs.s_id = s_id[g];
+        gs.s_fill = s_fill[g];
+        gs.s_next = &s_next[g];
+        gs.s_flag = &s_gflag[g];
+        gs.g = g;
+        uint32_t seq = 0;
+        for (uint32_t b = 0; b < p.n_buckets; ++b) {
+            if (t == 0) {  // the group goes on once the reducers are close enough behind
+                uint32_t go = 0;
+                for (uint32_t k = 0; k < kSpinLimit && !*fail; ++k)
+                    if (*reduced + kSortAhead > b) {
+                        go = 1;
+                        break;
+                    }
+                if (!go && !*fail) {
+                    latch_status(status, SINET_ERR_TIMEOUT);
+                    *fail = 1;
+                }
+                s_go[g] = go && !*fail;
+            }
+            group_sync(g);
+            if (!reinterpret_cast<volatile uint32_t *>(s_go)[g]) break;
+            if (!sort_pages(p, gs, b, seq, status)) {
+                *fail = 1;
+                break;
+            }
+        }
+    } else {
+        const uint32_t t = threadIdx.x - NS;
+        for (uint32_t b = 0; b < p.n_buckets; ++b) {
+            if (!reduce_bucket<NR>(h, p, tile, b, SG, accumulate, &s_ok, &s_fail, t, status)) {
+                *fail = 1;
+                break;
+            }
+            if (t == 0) *reduced = b + 1;
+        }
     }
+    __syncthreads();
 }
 
 // 6. Hot totals into their bins (a replicated bin sits in four slots, so
@@ -1012,12 +1051,12 @@ cudaError_t plan_partition(int lk, uint32_t table_smem, const RecArgs &r, const 
     const uint32_t nb = (uint32_t)(((uint64_t)h.n_bins + (1ull << cb) - 1) >> cb);
     const uint32_t T = (uint32_t)(((1ull << cb) + G - 1) / G);
     // two page-sorting groups where the tile leaves room, else one
-    // four page-sorting groups where the tile leaves room, else two or one
-    // (1 KB for the kernel's static shared memory)
+    // two page-sorting groups where the tile leaves room, else one (1 KB for
+    // the kernel's static shared memory)
     const size_t group = cold_group_bytes(G);
     const size_t tail = 24ull * T;
-    P.cold_groups = 4;
-    while (P.cold_groups > 1 && P.cold_groups * group + tail + 1024 > smem_optin) P.cold_groups /= 2;
+    P.cold_groups = 2;
+    while (P.cold_groups > 1 && P.cold_groups * group + tail + 1024 > smem_optin) P.cold_groups -= 1;
     P.smem_cold = P.cold_groups * group + tail;
     if (P.smem_cold + 1024 > smem_optin) return cudaErrorNotSupported;
     // hot table: as many sets as shared memory allows (at least 2^4)
@@ -1192,9 +1231,7 @@ cudaError_t run_partition(int lk, const RecArgs &r, const TableArgs &t, const Hi
     HistArgs hh = h;
     uint32_t *status = c.status;
     void *args[] = {&hh, &d, &acc, &status};
-    const void *cold = P.cold_groups == 4   ? (const void *)k_part_cold<4>
-                       : P.cold_groups == 2 ? (const void *)k_part_cold<2>
-                                            : (const void *)k_part_cold<1>;
+    const void *cold = P.cold_groups == 2 ? (const void *)k_part_cold<2> : (const void *)k_part_cold<1>;
     if ((e = cudaFuncSetAttribute(cold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem_cold)) !=
         cudaSuccess)
         return e;

@@ -13,11 +13,11 @@
 //      (bin << 1 | direction, bytes) appended to a CTA-private page of its
 //      coarse bin range (a bucket);
 //   4. pages are grouped by bucket;
-//   5. cold pass (one cooperative launch): for each bucket in turn, the
-//      CTAs' page-sorting groups take the bucket's pages one at a time and
-//      sort each by owner CTA in place (the pages stay in L2), then each CTA
-//      sums its own slice of the bucket's bins in a shared-memory tile and
-//      stores every bin of the slice once;
+//   5. cold pass (one cooperative launch): the CTAs' page-sorting groups take
+//      each bucket's pages one at a time and sort each by owner CTA in place
+//      (the pages stay in L2); behind them, each CTA's reducing warps sum its
+//      own slice of the bucket's bins in a shared-memory tile and store every
+//      bin of the slice once;
 //   6. the hot table's totals are added to their bins.
 // Every update is counted exactly once: in a hot slot or as a cold entry.
 #pragma once
@@ -93,7 +93,7 @@ struct PartPlan {
     PartDev d;                 // pointers filled once the scratch exists
     uint32_t slots;            // 4 << set_bits
     int grid_main, grid_sample, grid_cold;
-    int cold_groups;           // page-sorting groups in a 1,024-thread cold-pass CTA (1, 2 or 4)
+    int cold_groups;           // page-sorting groups of 256 threads in a 1,024-thread cold-pass CTA (1 or 2)
     size_t smem_main, smem_sample, smem_cold;
     size_t scratch_bytes;
     // scratch layout (byte offsets)

@@ -1,8 +1,9 @@
 """GPU parity of the hot/cold partitioned update (SINET_STRAT_PARTITION)
 against the oracle, on the paths the generic strategy tests do not reach:
-buckets that fill many pages per CTA, outputs that start as garbage (every
-bin is stored once), bucket sizes set by tile_bins, unaligned streams with
-whole TMA stages, the two-direction policy, and the refused combinations.
+buckets that fill many pages per CTA (beyond the CTA's own page region),
+outputs that start as garbage (every bin is stored once), bucket sizes set by
+tile_bins, unaligned streams with whole TMA stages, the two-direction policy,
+and the refused combinations.
 """
 from __future__ import annotations
 
@@ -51,6 +52,7 @@ def _uniform(n, n_bins, seed, t0=0, width=1):
 
 @pytest.mark.parametrize("n,n_bins,tile_bins", [
     (3_000_001, 524_288, 0),          # one bucket, ~99 % cold: several pages per CTA
+    (8_000_003, 524_288, 0),          # one bucket: each CTA's region overflows into pages taken on demand
     (2_500_003, 3_000_000, 1 << 16),  # 46 buckets of 2^16 bins
     (1_200_007, 40_000_000, 1 << 20), # 39 buckets of 2^20 bins (the largest tile)
 ])
