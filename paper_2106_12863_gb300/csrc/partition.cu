@@ -666,8 +666,10 @@ constexpr uint32_t kSortAhead = 8;       // buckets the sorting groups may run a
 // next page lands in one while the page in the other is sorted in place) and
 // the owner counts of each.
 struct GroupSmem {
-    uint64_t *buf[2];   // [kPartPage]
-    uint32_t *ocnt[2];  // [cold_ocnt_words] owner counts, then run offsets
+    uint64_t *buf;      // [2][kPartPage] (addressed by offset, never by a runtime array index,
+                        // which would put the struct in local memory)
+    uint32_t *ocnt;     // [2][ow] owner counts, then run offsets
+    uint32_t ow;        // words of one owner-count array
     uint64_t *bar;      // [2] page copies
     uint32_t *s_id;     // [2] page id of the copy in flight into buf[k]
     uint32_t *s_fill;   // [2] its entries
@@ -695,7 +697,7 @@ __device__ __forceinline__ void issue_page(const PartDev &p, const GroupSmem &gs
     const uint32_t bar = smem_u32(gs.bar + k);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier accesses of buf[k] first
     mbar_expect_tx(bar, bytes);
-    if (bytes) bulk_g2s(smem_u32(gs.buf[k]), p.pages + (uint64_t)id * kPartPage, bytes, bar);
+    if (bytes) bulk_g2s(smem_u32(gs.buf + k * kPartPage), p.pages + (uint64_t)id * kPartPage, bytes, bar);
 }
 
 // The group's thread 0: claim bucket b's next unsorted page and start its
@@ -710,9 +712,9 @@ __device__ __forceinline__ uint32_t claim_page(const PartDev &p, const GroupSmem
 // This group's pages of bucket b, each sorted by owner in place with its
 // owner run offsets recorded (its row of idx), then the group counts itself
 // done with the bucket. Four group barriers per page: the copy has landed;
-// owners counted; offsets scanned; entries scattered (the copy of the next
-// page, into the other buffer, starts after the first). `seq` counts the
-// group's pages over all buckets (buffer and phase). Returns false when a
+// owners counted; offsets scanned; entries scattered (the claim and copy of
+// the next page, into the other buffer, run during the scan). `seq` counts
+// the group's pages over all buckets (buffer and phase). Returns false when a
 // page copy's wait ran out.
 __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t &seq,
                                            uint32_t *status) {
@@ -732,11 +734,9 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
             if (tid == 0) latch_status(status, SINET_ERR_TIMEOUT);
             return false;
         }
-        // the other buffer's page was stored back before the barrier: the next copy may land there
-        if (tid == 0) *s_next = claim_page(p, gs, b, k ^ 1u);
         const uint32_t id = gs.s_id[k], fill = gs.s_fill[k];
-        uint64_t *pg = gs.buf[k];
-        uint32_t *oc = gs.ocnt[k];
+        uint64_t *pg = gs.buf + k * kPartPage;
+        uint32_t *oc = gs.ocnt + k * gs.ow;
         uint64_t ent[U];
         uint32_t pos[U];  // owner << 16 | rank among the owner's entries
 #pragma unroll
@@ -752,9 +752,13 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
         }
         // the next page's counts start from zero (the last page that used
         // them wrote its row before the barrier above)
-        uint32_t *on = gs.ocnt[k ^ 1u];
+        uint32_t *on = gs.ocnt + (k ^ 1u) * gs.ow;
         for (uint32_t o = tid; o <= G; o += GT) on[o] = 0;
         group_sync(gs.g);
+        // while the first warp scans: the next page's claim and copy (into
+        // the other buffer, whose page was stored back before the first
+        // barrier) by the second warp, off the group's barrier-to-barrier path
+        if (tid == 32) *s_next = claim_page(p, gs, b, k ^ 1u);
         // exclusive scan of the G + 1 counts by the group's first warp (the
         // last count is always zero, so its offset is the page's fill)
         if (tid < 32) {
@@ -953,10 +957,9 @@ __global__ void __launch_bounds__(kColdThreads, 1) k_part_cold(HistArgs h, PartD
     if (threadIdx.x < NS) {
         const uint32_t g = threadIdx.x / kSortThreads, t = threadIdx.x % kSortThreads;
         GroupSmem gs;
-        gs.buf[0] = reinterpret_cast<uint64_t *>(smem + g * cold_group_bytes(p.g_cold));
-        gs.buf[1] = gs.buf[0] + kPartPage;
-        gs.ocnt[0] = reinterpret_cast<uint32_t *>(gs.buf[1] + kPartPage);
-        gs.ocnt[1] = gs.ocnt[0] + ow;
+        gs.buf = reinterpret_cast<uint64_t *>(smem + g * cold_group_bytes(p.g_cold));
+        gs.ocnt = reinterpret_cast<uint32_t *>(gs.buf + 2 * kPartPage);
+        gs.ow = ow;
         gs.bar = s_bar[g];
         gs.s_id = s_id[g];
         gs.s_fill = s_fill[g];
