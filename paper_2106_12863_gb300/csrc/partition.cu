@@ -344,13 +344,16 @@ __device__ __forceinline__ void part_record(const HistArgs &h, const PartDev &p,
 
 // The staged path's pieces, for two records per thread and warp-wide steps.
 
-// Hot-table slot of a bin, or kNoKey.
+// Hot-table slot of a bin, or kNoKey, without branches: w has bit i set
+// when way i holds the bin; a replicated set (all four ways hold one of the
+// very hottest bins) spreads its lanes over the four copies.
 __device__ __forceinline__ uint32_t hot_slot(const MainSmem &m, uint32_t bin) {
     const uint32_t set = fib_hash(bin) >> m.shift;
     const uint4 k4 = *reinterpret_cast<const uint4 *>(m.hkeys + 4 * set);
-    if (k4.x == bin && k4.w == bin) return 4 * set + (threadIdx.x & 3u);  // a replicated set
-    const int way = k4.x == bin ? 0 : k4.y == bin ? 1 : k4.z == bin ? 2 : k4.w == bin ? 3 : -1;
-    return way < 0 ? kNoKey : 4 * set + (uint32_t)way;
+    const uint32_t w = (uint32_t)(k4.x == bin) | (uint32_t)(k4.y == bin) << 1 | (uint32_t)(k4.z == bin) << 2 |
+                       (uint32_t)(k4.w == bin) << 3;
+    const uint32_t way = w == 15u ? (threadIdx.x & 3u) : (uint32_t)(__ffs(w) - 1);
+    return w ? 4 * set + way : kNoKey;
 }
 
 __device__ __forceinline__ void hot_add(const MainSmem &m, uint32_t slot, uint32_t d, uint32_t by) {
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
             for (int j = 0; j < 2; ++j)
                 if (slot[j] != kNoKey) hot_add(m, slot[j], first_dir(dirs[j]), by[j]);
             // classes routed to both directions: the second one
-            if (__any_sync(kFull, dirs[0] == 3u || dirs[1] == 3u)) {
+            if (h.two_dir && __any_sync(kFull, dirs[0] == 3u || dirs[1] == 3u)) {
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     if (dirs[j] != 3u) continue;
