@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
                 break;
             }
             uint32_t in[4];
-            C.template in_n<4>(a, in);
+            C.template in_n_warp<4>(a, in);  // the warp is converged here
             uint32_t bin[2], dirs[2], slot[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {

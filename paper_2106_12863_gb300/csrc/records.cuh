@@ -67,6 +67,30 @@ struct ToggleClassifier {
     __device__ __forceinline__ void in_n(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
         v.template contains_n<N>(a, r);
     }
+    // in_n for a whole converged warp: when no lane's address falls in a
+    // bucket with blocks (the common case: most buckets are pure), the
+    // descriptors' parity bits are the answers and one vote replaces the
+    // per-lookup block branches.
+    template <int N>
+    __device__ __forceinline__ void in_n_warp(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
+        if (NB == 0) {  // every bucket has a block
+            v.template contains_n<N>(a, r);
+            return;
+        }
+        constexpr uint32_t kBlocks = NB == 2 ? 0x3FFFFFFFu : 0x7FFFu;
+        uint32_t d[N], any = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            d[i] = v.desc[a[i] >> v.shift];
+            any |= d[i] & kBlocks;
+        }
+        if (__any_sync(kFull, any)) {
+            v.template contains_n<N>(a, r);
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[i] = d[i] >> 31;
+    }
 };
 template <>
 struct Classifier<LK_INTERVAL> : ToggleClassifier<0> {};
@@ -92,6 +116,10 @@ struct Classifier<LK_PML> {
 #pragma unroll
         for (int i = 0; i < N; ++i) r[i] = v.contains(a[i]);
     }
+    template <int N>
+    __device__ __forceinline__ void in_n_warp(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
+        in_n<N>(a, r);
+    }
 };
 
 template <>
@@ -113,6 +141,10 @@ struct Classifier<LK_INTERVAL_GLOBAL> {
     __device__ __forceinline__ void in_n(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
 #pragma unroll
         for (int i = 0; i < N; ++i) r[i] = v.contains(a[i]);
+    }
+    template <int N>
+    __device__ __forceinline__ void in_n_warp(const uint32_t (&a)[N], uint32_t (&r)[N]) const {
+        in_n<N>(a, r);
     }
 };
 
