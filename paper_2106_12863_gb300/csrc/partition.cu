@@ -475,26 +475,29 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
         uint32_t cc8 = 0;   // per-thread class counts, 8-bit fields
         uint32_t oorp = 0;  // per-thread out-of-window counts, 16-bit fields
         uint32_t since = 0;
-        // two stages per iteration: record j of this thread comes from chunk q + j
-        for (uint64_t q = 0;; q += 2) {
+        // one stage per iteration: records 2 * tid and 2 * tid + 1 of the chunk
+        static_assert(kPartRPT == 2, "two records per consumer thread and stage");
+        for (uint64_t q = 0;; ++q) {
             const uint64_t ch0 = blockIdx.x + q * gridDim.x;
             if (ch0 >= p.n_full) break;
-            const bool has1 = ch0 + gridDim.x < p.n_full;  // warp-uniform
             uint64_t ts[2] = {0, 0};
-            uint32_t a[4] = {0, 0, 0, 0}, by[2] = {0, 0};
-            bool ok = true;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (j == 1 && !has1) break;
-                const uint64_t qq = q + (uint64_t)j;
-                const uint32_t s = (uint32_t)(qq % kPartStages);
-                ok = __all_sync(kFull, mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(qq / kPartStages) & 1u));
-                if (!ok) break;
+            uint32_t a[4] = {0, 0, 0, 0}, by[2] = {0, 0};  // a: src, dst of record 0, then of record 1
+            const uint32_t s = (uint32_t)(q % kPartStages);
+            const bool ok = __all_sync(kFull, mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(q / kPartStages) & 1u));
+            if (ok) {
                 const uint8_t *sp = stage + s * kPartStageBytes;
-                ts[j] = *reinterpret_cast<const uint64_t *>(sp + 8 * tid);
-                a[2 * j] = *reinterpret_cast<const uint32_t *>(sp + 8 * R + 4 * tid);
-                a[2 * j + 1] = *reinterpret_cast<const uint32_t *>(sp + 12 * R + 4 * tid);
-                by[j] = *reinterpret_cast<const uint32_t *>(sp + 16 * R + 4 * tid);
+                const uint4 t2 = *reinterpret_cast<const uint4 *>(sp + 16 * tid);
+                const uint2 s2 = *reinterpret_cast<const uint2 *>(sp + 8 * R + 8 * tid);
+                const uint2 d2 = *reinterpret_cast<const uint2 *>(sp + 12 * R + 8 * tid);
+                const uint2 b2 = *reinterpret_cast<const uint2 *>(sp + 16 * R + 8 * tid);
+                ts[0] = (uint64_t)t2.y << 32 | t2.x;
+                ts[1] = (uint64_t)t2.w << 32 | t2.z;
+                a[0] = s2.x;
+                a[1] = d2.x;
+                a[2] = s2.y;
+                a[3] = d2.y;
+                by[0] = b2.x;
+                by[1] = b2.y;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
             }
@@ -510,13 +513,12 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_main(RecArgs r, TableA
             uint32_t bin[2], dirs[2], slot[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const bool valid = j == 0 || has1;
                 const uint32_t cls = in[2 * j] | in[2 * j + 1] << 1;
-                if (valid) cc8 += 1u << (8 * cls);
+                cc8 += 1u << (8 * cls);
                 const uint64_t rel = ts[j] - h.t0;
                 const bool inw = rel < h.span;
                 bin[j] = inw ? (W1 ? (uint32_t)rel : (uint32_t)divide(rel, h.div)) : 0u;
-                uint32_t d = valid ? (h.policy >> (8 * cls)) & 3u : 0u;
+                uint32_t d = (h.policy >> (8 * cls)) & 3u;
                 if (!inw) {
                     oorp += (d & 1u) | ((d >> 1) << 16);
                     d = 0;

@@ -26,14 +26,15 @@
 namespace sinet {
 
 // Main pass: 31 consumer warps and one producer warp, 1,024 threads (64
-// registers each fit the register file), one record per consumer per stage.
+// registers each fit the register file), two adjacent records per consumer
+// per stage (read with one 16-byte and three 8-byte shared-memory loads), two
+// stages of 39 KB in flight.
 constexpr int kPartConsumers = 992;                 // consumer threads of the main pass
 constexpr int kPartThreads = kPartConsumers + 32;   // plus one producer warp (TMA)
-constexpr int kPartRPT = 1;                         // records per consumer per stage (1 or 2)
+constexpr int kPartRPT = 2;                         // records per consumer per stage
 constexpr uint32_t kPartStageRecords = kPartRPT * kPartConsumers;  // records per TMA stage
-static_assert(kPartRPT == 1 || kPartRPT == 2, "one or two records per consumer thread and stage");
 static_assert((4 * kPartStageRecords) % 16 == 0, "every stage starts 16-byte aligned in every stream");
-constexpr uint32_t kPartStages = 4;
+constexpr uint32_t kPartStages = 2;
 constexpr uint32_t kPartStageBytes = 20 * kPartStageRecords;
 constexpr uint32_t kPartPageBits = 11;              // 2,048 entries (16 KB) per page
 constexpr uint32_t kPartPage = 1u << kPartPageBits;
