@@ -692,6 +692,17 @@ __device__ __forceinline__ void reduce_sync() {
     asm volatile("bar.sync %0, %1;" ::"n"(kReduceBar), "n"(NR) : "memory");
 }
 
+// Exclusive prefix sum of v across the (converged) warp.
+__device__ __forceinline__ uint32_t warp_exclusive(uint32_t v, uint32_t lane) {
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
+    }
+    return incl - v;
+}
+
 // The group's thread 0: start the TMA copy of the page at list position j into buf[k].
 __device__ __forceinline__ void issue_page(const PartDev &p, const GroupSmem &gs, uint32_t j, uint32_t k) {
     const uint32_t id = p.page_list[j];
@@ -768,21 +779,30 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
         // last count is always zero, so its offset is the page's fill)
         if (tid < 32) {
             const uint32_t per = (G + 1 + 31) / 32, o0 = lane * per;
-            uint32_t sum = 0;
-            for (uint32_t q = 0; q < per; ++q)
-                if (o0 + q <= G) sum += oc[o0 + q];
-            uint32_t incl = sum;
+            if (per <= 8) {  // up to 255 owners: each lane's counts stay in registers
+                uint32_t c[8], sum = 0;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, incl, d);
-                if (lane >= (uint32_t)d) incl += y;
-            }
-            uint32_t ex = incl - sum;
-            for (uint32_t q = 0; q < per; ++q) {
-                if (o0 + q > G) break;
-                const uint32_t c = oc[o0 + q];
-                oc[o0 + q] = ex;
-                ex += c;
+                for (uint32_t q = 0; q < 8; ++q) {
+                    c[q] = (q < per && o0 + q <= G) ? oc[o0 + q] : 0u;
+                    sum += c[q];
+                }
+                uint32_t ex = warp_exclusive(sum, lane);
+#pragma unroll
+                for (uint32_t q = 0; q < 8; ++q) {
+                    if (q < per && o0 + q <= G) oc[o0 + q] = ex;
+                    ex += c[q];
+                }
+            } else {
+                uint32_t sum = 0;
+                for (uint32_t q = 0; q < per; ++q)
+                    if (o0 + q <= G) sum += oc[o0 + q];
+                uint32_t ex = warp_exclusive(sum, lane);
+                for (uint32_t q = 0; q < per; ++q) {
+                    if (o0 + q > G) break;
+                    const uint32_t c = oc[o0 + q];
+                    oc[o0 + q] = ex;
+                    ex += c;
+                }
             }
         }
         group_sync(gs.g);
@@ -817,7 +837,7 @@ __device__ __forceinline__ bool sort_pages(const PartDev &p, const GroupSmem &gs
 // low words of both, high words of both. Each warp takes a contiguous share
 // of the bucket's pages, 32 at a time (one per lane): it reads their run
 // bounds, scans the run lengths across the warp, and walks the concatenated
-// runs 32 entries per step, four steps of loads in flight; a lane finds the
+// runs 32 entries per step, eight steps of loads in flight; a lane finds the
 // run of its entry by binary search over the warp's run starts (the last run
 // starting at or before the entry holds it, empty runs included).
 template <uint32_t NR>
@@ -861,10 +881,10 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
             if (lane >= (uint32_t)d) incl += y;
         }
         const uint32_t start = incl - len, total = __shfl_sync(kFull, incl, 31);
-        for (uint32_t k0 = 0; k0 < total; k0 += 4 * 32) {
-            uint64_t e[4];
+        for (uint32_t k0 = 0; k0 < total; k0 += 8 * 32) {
+            uint64_t e[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const uint32_t k = k0 + (uint32_t)u * 32 + lane;
                 uint32_t r = 0;
 #pragma unroll
@@ -875,7 +895,7 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
                 e[u] = k < total ? p.pages[a + (k - sr)] : 0ull;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 if (k0 + (uint32_t)u * 32 + lane >= total) continue;
                 const uint32_t key = (uint32_t)(e[u] >> 32);
                 const uint32_t d = key & 1u;
