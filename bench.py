@@ -1010,10 +1010,10 @@ def run_window_bench(args, w, rank, world, dev, extras: bool):
                                    + ("the library call" if own else "output zeroing + the library call")}
     # kernels per step: one fused kernel (zeroing is cudaMemsetAsync), plus
     # the cell expansion for the cell strategy; the run boundaries, their scan
-    # and the remainder for the owner strategy; sample, levels, candidates,
-    # hot table, main pass, three page-grouping kernels, cold pass and hot
-    # totals for the partition
-    result["gpu_launches"] = args.steps * {"atomic_cell": 2, "owner": 4, "partition": 10}.get(strategy, 1)
+    # and the remainder for the owner strategy; sample, levels, total,
+    # candidates, hot table, main pass, three page-grouping kernels, cold pass
+    # and hot totals for the partition
+    result["gpu_launches"] = args.steps * {"atomic_cell": 2, "owner": 4, "partition": 11}.get(strategy, 1)
     result["config"] = {"workload": w.name, "records": n, "prefixes": w.table.n,
                         "n_bins": w.n_bins, "bin_width_ms": w.bin_width, "strategy": strategy,
                         "tune_ms": tune, "l2": f"inputs larger than L2 ({RECORD_BYTES * n / 1e9:.1f} GB of records)",

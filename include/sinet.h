@@ -98,11 +98,13 @@ typedef enum {
                                       until there are at most 256 ranges; at most 2^20).
                                       sinet_discriminate_histogram only, no watch list; at most
                                       2^32 - 4,096 routed updates and 2^28 bins. Scratch, stream-
-                                      ordered: 16 KB pages of 2,048 entries for every routed
-                                      update (8 bytes each) plus two pages per CTA and range,
-                                      about 320 bytes of bookkeeping per page, and 64 MB at most
-                                      for the sample. The second kernel is a cooperative launch
-                                      (one CTA per SM, all resident). */
+                                      ordered: 16 KB pages of 2,048 entries, namely a region
+                                      per CTA and range (pages for an even share of 30 % of the
+                                      routed updates, plus one, at most 16) and a shared pool for
+                                      every routed update (8 bytes each) plus two pages per CTA
+                                      and range; about 320 bytes of bookkeeping per page, and
+                                      64 MB at most for the sample. The second kernel is a
+                                      cooperative launch (one CTA per SM, all resident). */
 } sinet_strategy;
 
 /* How membership is looked up. Both are exact. */
@@ -524,9 +526,11 @@ sinet_status sinet_histogram_sparse(const sinet_hist_out *in, uint64_t n_bins, u
  * with these parameters over n records would run: p->strategy unless it is
  * AUTO; for AUTO, the measured choice cached for the call's input class
  * (SINET_HINT_TUNE) or else the fixed rule (the whole-histogram tile for
- * small histograms, the chunk tile for time-sorted input, the 32-byte cells
- * for unsorted input over a histogram of 256 MB or more, warp combining
- * otherwise). No kernel runs.
+ * small histograms, the chunk tile for time-sorted input, the hot/cold
+ * partition for unsorted input over a histogram of 256 MB or more with at
+ * least one record per four bins (the 32-byte cells where the partition's
+ * limits are exceeded, or where its scratch does not fit the free device
+ * memory at the call), warp combining otherwise). No kernel runs.
  */
 sinet_status sinet_auto_strategy(const sinet_prefix_table *t, uint64_t n, const sinet_hist_params *p,
                                  int32_t *strategy);

@@ -193,13 +193,36 @@ static uint32_t tile_capacity_pair(const DeviceState *ds, uint32_t tsm) {
 // What AUTO runs without a measurement: the whole-histogram tile for small
 // histograms, the chunk tile for time-sorted input, the cells for unsorted
 // input over a histogram far beyond L2, warp combining otherwise.
-static int auto_rule(const sinet_hist_params *p, const RecArgs &r, uint32_t cap) {
+// The cell strategy: zeroed cells, the combining kernel into them, then the
+// expansion into the outputs.
+static cudaError_t run_cells(int lk, const RecArgs &r, const TableArgs &ta_tab, HistArgs h,
+                             const sinet_hist_params *p, const LaunchCfg &c, cudaStream_t s,
+                             const TableArgs *watch = nullptr) {
+    const size_t cell_bytes = 32 * (size_t)p->n_bins;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&h.cells), cell_bytes, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(h.cells, 0, cell_bytes, s);
+    if (e == cudaSuccess) e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c, watch);
+    if (e == cudaSuccess) e = run_cells_expand(h, p->accumulate != 0, c);
+    const cudaError_t e2 = cudaFreeAsync(h.cells, s);
+    return e == cudaSuccess ? e2 : e;
+}
+
+static int auto_rule(const sinet_hist_params *p, const RecArgs &r, uint32_t cap, int lk, uint32_t tsm,
+                     const HistArgs &h, const DeviceState *ds) {
     if (2ull * p->n_bins <= 8192 && p->n_bins <= cap) return SINET_STRAT_SMEM_FULL;
     // the tile strategy: measured faster than OWNER on the paper-shaped day
     // (about 4.6 records per ms bin, +-500 ms disorder)
     if (p->hints & SINET_HINT_TIME_SORTED) return SINET_STRAT_PRIV_TILE;
-    // measured faster than the hot/cold partition on the Zipf-skewed heavy day
-    if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4) return SINET_STRAT_ATOMIC_CELL;
+    // unsorted input over a histogram far beyond L2: the hot/cold partition
+    // (measured 1.9x faster than the cells on the Zipf-skewed heavy day),
+    // else the cells
+    if (24 * p->n_bins >= kCellMinHistBytes && r.g.n >= p->n_bins / 4) {
+        PartPlan probe{};
+        if (plan_partition(lk, tsm, r, h, 0, ds->sm_count, ds->smem_optin, &probe) == cudaSuccess)
+            return SINET_STRAT_PARTITION;
+        return SINET_STRAT_ATOMIC_CELL;
+    }
     return SINET_STRAT_GLOBAL_ATOMIC;
 }
 
@@ -313,7 +336,7 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
     // a watch list keeps few records (a blocklist): the plain combining kernel
     if (strat == SINET_STRAT_AUTO && watch) strat = SINET_STRAT_GLOBAL_ATOMIC;
     if (strat == SINET_STRAT_AUTO) {
-        strat = auto_rule(p, r, cap);
+        strat = auto_rule(p, r, cap, lk, tsm, h, ds);
         int dev = 0;
         cudaGetDevice(&dev);
         const std::string key = auto_key(dev, lk, p, r, h);
@@ -419,18 +442,9 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         case SINET_STRAT_ATOMIC_NOAGG:
             e = run_fused_atomic(lk, false, r, ta_tab, h, 0, c, watch);
             break;
-        case SINET_STRAT_ATOMIC_CELL: {
-            // zeroed cells, the combining kernel into them, then the expansion
-            const size_t cell_bytes = 32 * (size_t)p->n_bins;
-            e = cudaMallocAsync(reinterpret_cast<void **>(&h.cells), cell_bytes, s);
-            if (e != cudaSuccess) return cuda_fail(e);
-            e = cudaMemsetAsync(h.cells, 0, cell_bytes, s);
-            if (e == cudaSuccess) e = run_fused_atomic(lk, true, r, ta_tab, h, kCacheSetBits, c, watch);
-            if (e == cudaSuccess) e = run_cells_expand(h, p->accumulate != 0, c);
-            const cudaError_t e2 = cudaFreeAsync(h.cells, s);
-            if (e == cudaSuccess) e = e2;
+        case SINET_STRAT_ATOMIC_CELL:
+            e = run_cells(lk, r, ta_tab, h, p, c, s, watch);
             break;
-        }
         case SINET_STRAT_PRIV_TILE:
         case SINET_STRAT_SMEM_FULL:
             e = run_fused_tile(lk, r, ta_tab, h, ta, ct);
@@ -450,6 +464,13 @@ static sinet_status run_hist(const sinet_prefix_table *t, int lk, const RecArgs 
         case SINET_STRAT_PARTITION: {
             void *scratch = nullptr;
             e = cudaMallocAsync(&scratch, pplan.scratch_bytes, s);
+            if (e != cudaSuccess && p->strategy == SINET_STRAT_AUTO) {
+                // AUTO's choice does not fit the free memory: the cells need
+                // far less scratch and zero the same outputs (none)
+                cudaGetLastError();
+                e = run_cells(lk, r, ta_tab, h, p, c, s);
+                break;
+            }
             if (e != cudaSuccess) return cuda_fail(e);
             e = run_partition(lk, r, ta_tab, h, pplan, scratch, p->accumulate != 0, c);
             const cudaError_t e2 = cudaFreeAsync(scratch, s);
@@ -721,7 +742,8 @@ sinet_status sinet_auto_strategy(const sinet_prefix_table *t, uint64_t n, const 
     r.g.n = n;
     sinet_hist_out o{};
     HistArgs h = make_hist(p, &o);
-    *strategy = auto_rule(p, r, tile_capacity(ds, table_smem(t, lk)));
+    const uint32_t tsm = table_smem(t, lk);
+    *strategy = auto_rule(p, r, tile_capacity(ds, tsm), lk, tsm, h, ds);
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk_(g_auto_mu);
