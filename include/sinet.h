@@ -85,7 +85,7 @@ typedef enum {
                                       512 threads per block. */
     SINET_STRAT_PARTITION = 8      /* hot/cold partition, for unsorted input over histograms far
                                       larger than L2 (Section 5's map-reduce with the reduction
-                                      kept on chip): a strided sample of about n / 2,048 records
+                                      kept on chip): a strided sample of about n / 4,096 records
                                       ranks the bins; the most sampled ones (up to 16,384 slots,
                                       as shared memory allows) are summed in shared memory by
                                       every CTA; every other routed update is appended as an

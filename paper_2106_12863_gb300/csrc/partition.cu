@@ -1094,10 +1094,10 @@ cudaError_t plan_partition(int lk, uint32_t table_smem, const RecArgs &r, const 
     if (main_smem(tsm, 4u << sb, nb) + 1024 > smem_optin) return cudaErrorNotSupported;
     P.slots = 4u << sb;
     P.smem_main = main_smem(tsm, P.slots, nb);
-    // sample: about n / 2048 records (at least 2^20, at most all), in chunks;
-    // bins holding 1 / 100,000 of the updates still get tens of hits
+    // sample: about n / 4096 records (at least 2^19, at most all), in chunks;
+    // bins holding 1 / 50,000 of the updates still get about ten hits
     const uint64_t chunks = (n + kPartSampleChunk - 1) / kPartSampleChunk;
-    const uint64_t target = std::min<uint64_t>(n, std::max<uint64_t>(1ull << 20, n >> 11));
+    const uint64_t target = std::min<uint64_t>(n, std::max<uint64_t>(1ull << 19, n >> 12));
     uint64_t stride = target ? (chunks * kPartSampleChunk) / target : 1;
     if (stride < 1) stride = 1;
     const uint64_t s_chunks = (chunks + stride - 1) / stride;
