@@ -857,8 +857,7 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
         if (!ok) latch_status(status, SINET_ERR_TIMEOUT);
         *s_ok = ok ? 1u : 0u;
     }
-    for (uint32_t i = tid; i < 6 * T; i += NR) tile[i] = 0;
-    reduce_sync<NR>();
+    reduce_sync<NR>();  // the tile was zeroed by the previous bucket's store (or at the start)
     if (!*s_ok) return false;
     const uint64_t lo_bin = ((uint64_t)b << p.cb_shift) + (uint64_t)o * T;
     const uint32_t warp = tid >> 5, lane = tid & 31, nw = NR >> 5;
@@ -921,6 +920,8 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
             uint32_t c0 = tile[i], c1 = tile[T + i];
             uint64_t s0 = (uint64_t)tile[4 * T + i] << 32 | tile[2 * T + i];
             uint64_t s1 = (uint64_t)tile[5 * T + i] << 32 | tile[3 * T + i];
+#pragma unroll
+            for (uint32_t k = 0; k < 6; ++k) tile[k * T + i] = 0;  // ready for the next bucket
             if (accumulate) {
                 c0 += h.cnt[0][bin];
                 c1 += h.cnt[1][bin];
@@ -933,7 +934,7 @@ __device__ __forceinline__ bool reduce_bucket(const HistArgs &h, const PartDev &
             h.byt[1][bin] = s1;
         }
     }
-    reduce_sync<NR>();  // the tile is zeroed for the next bucket after every store
+    reduce_sync<NR>();  // every bin stored and zeroed before the next bucket's adds
     return true;
 }
 
@@ -962,6 +963,7 @@ __global__ void __launch_bounds__(kColdThreads, 1) k_part_cold(HistArgs h, PartD
     __shared__ uint64_t s_bar[SG][2];
     const uint32_t ow = cold_ocnt_words(p.g_cold);
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem + SG * cold_group_bytes(p.g_cold));
+    for (uint32_t i = threadIdx.x; i < 6 * p.own_bins; i += kColdThreads) tile[i] = 0;
     if (threadIdx.x < NS) {  // both owner-count arrays of every group start at zero
         uint32_t *oc = reinterpret_cast<uint32_t *>(smem + (threadIdx.x / kSortThreads) * cold_group_bytes(p.g_cold) +
                                                     16ull * kPartPage);
