@@ -349,3 +349,18 @@ def test_auto_measured_choice(orc, key, hints):
     assert sinet.auto_strategy(t, n, sinet.HistParams(w.t0, w.bin_width, w.n_bins, hints=hints)) == chosen
     again = run_fused(t, d, p)  # cached: no timing
     assert_hist_equal(again, ref, f"auto measured (cached {chosen})")
+
+
+def test_auto_rule_by_input_class():
+    # the fixed rule (no kernel runs): the partition for unsorted input over a
+    # large histogram with at least one record per four bins, the chunk tile
+    # for time-sorted input, warp combining for sparse input
+    w = gen.WORKLOADS["heavy"]
+    net, ln = gen.make_table(w.table, w.seed)
+    t = sinet.PrefixTable(net, ln)
+    p = sinet.HistParams(w.t0, w.bin_width, w.n_bins)
+    assert sinet.auto_strategy(t, w.records.n, p) == "partition"
+    assert sinet.auto_strategy(t, w.records.n, sinet.HistParams(w.t0, w.bin_width, w.n_bins,
+                                                                 hints=sinet.HINT_TIME_SORTED)) == "priv_tile"
+    assert sinet.auto_strategy(t, w.n_bins // 8, p) == "global_atomic"
+    t.close()
