@@ -222,8 +222,14 @@ __global__ void __launch_bounds__(1024) k_part_build(PartDev p, uint32_t slots) 
         for (int k = 0; k < K; ++k) {
             if (key[k] == kNoKey || lev[k] != (uint32_t)l) continue;
             uint32_t *set = keys + 4 * (fib_hash(key[k]) >> shift);
-            for (int w = 0; w < 4; ++w)
-                if (atomicCAS(set + w, kNoKey, key[k]) == kNoKey) break;
+            bool placed = false;
+            for (int w = 0; w < 4 && !placed; ++w) placed = atomicCAS(set + w, kNoKey, key[k]) == kNoKey;
+            // a full set whose later ways repeat way 0 (a replicated bin)
+            // gives one of the copies up: a hot bin that shares its set with
+            // a replicated one must not fall to the cold path (way 0 keeps the
+            // replicated bin, whose probe then finds it there)
+            const uint32_t k0 = set[0];
+            for (int w = 3; w >= 1 && !placed && k0 != kNoKey; --w) placed = atomicCAS(set + w, k0, key[k]) == k0;
         }
         __syncthreads();
     }

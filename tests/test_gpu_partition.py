@@ -121,3 +121,22 @@ def test_refused_combinations():
             sinet.discriminate_histogram(t, d["ts"], d["src"], d["dst"], d["bytes"], p, o)
         assert e.value.status == status
         del o
+
+
+def test_hot_bins_sharing_a_replicated_set(orc):
+    # two very hot bins whose hot-table set is the same (the top 12 bits of
+    # bin * 0x9E3779B1 agree, so they share a set for every table size up to
+    # 2^12 sets): the hotter takes all four ways, the other one of its copies
+    n_bins, n = 524_288, 2_000_003
+    net, ln, rec = _uniform(n, n_bins, 13)
+    top = lambda b: ((b * 0x9E3779B1) & 0xFFFFFFFF) >> 20
+    a = 1234
+    b = next(x for x in range(n_bins) if x != a and top(x) == top(a))
+    u = np.random.default_rng(13).random(n)
+    ts = rec["ts"].copy()
+    ts[u < 0.4] = a
+    ts[(u >= 0.4) & (u < 0.6)] = b
+    rec["ts"] = ts.astype(np.uint64)
+    ref = orc.discriminate_histogram(net, ln, rec, 0, 1, n_bins)
+    got = _run(sinet.PrefixTable(net, ln), to_dev(rec), sinet.HistParams(0, 1, n_bins, strategy="partition"))
+    assert_hist_equal(got, ref, "two hot bins in one set")
