@@ -660,11 +660,12 @@ __global__ void __launch_bounds__(256) k_part_list_pages(PartDev p) {
 
 // ---------------------------------------------------------------------------
 // 5. Cold pass (cooperative: every CTA resident). CTA o owns bins
-// [o * own_bins, (o + 1) * own_bins) of every bucket. For each bucket b in
-// turn: sort_pages(b + 1), then reduce(b): the pages of the next bucket are
-// sorted while the other CTAs finish this one. A bucket's pages are handed
-// out one at a time from a per-bucket cursor to whichever page-sorting group
-// asks next, so every group ends its share of a bucket at about the same time.
+// [o * own_bins, (o + 1) * own_bins) of every bucket. Its page-sorting groups
+// sort the pages of bucket after bucket by owner, a bucket's pages handed out
+// one at a time from a per-bucket cursor to whichever group asks next (so
+// every group ends its share of a bucket at about the same time); its
+// reducing warps follow, summing bucket b once every group of every CTA has
+// sorted it (k_part_cold below).
 
 namespace {
 
