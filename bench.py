@@ -423,6 +423,16 @@ def run_batch_bench(args):
         slices.append((tables[i], d["ts"][a:a + n], d["src"][a:a + n], d["dst"][a:a + n],
                        d["bytes"][a:a + n], p, o))
     stream = torch.cuda.current_stream(dev)
+    # the tuner's choices per input class (strategy, ns per record) are read
+    # back from its cache file: a fresh one for this run unless the caller
+    # named one
+    tune_file, own_tune_file = os.environ.get("SINET_AUTOTUNE_CACHE"), False
+    if not tune_file:
+        import tempfile
+        fd, tune_file = tempfile.mkstemp(prefix="sinet_tune_", suffix=".txt")
+        os.close(fd)
+        os.environ["SINET_AUTOTUNE_CACHE"] = tune_file
+        own_tune_file = True
     tt = time.perf_counter()
     batch = sinet.Batch(slices, autotune=True)
     t_tune = time.perf_counter() - tt
@@ -431,6 +441,15 @@ def run_batch_bench(args):
     for i in range(len(plan)):
         s_ = batch.strategy(i)
         strat_count[s_] = strat_count.get(s_, 0) + 1
+    tuned = []
+    with open(tune_file) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3:
+                tuned.append({"class": parts[0], "strategy": parts[1], "ns_per_record": float(parts[2])})
+    if own_tune_file:
+        os.environ.pop("SINET_AUTOTUNE_CACHE", None)
+        os.unlink(tune_file)
 
     for _ in range(args.warmup):
         batch.run()
@@ -480,7 +499,7 @@ def run_batch_bench(args):
     name = f"batch-{len(plan)}-slices-uneven" + (f"-scale{args.scale:g}" if args.scale != 1.0 else "")
     result["config"] = {"workload": name, "records": n_tot,
                         "slices": len(plan), "bins_total": bins_tot, "work_items": items,
-                        "strategies": strat_count, "tune_s": round(t_tune, 2),
+                        "strategies": strat_count, "tune_s": round(t_tune, 2), "tuned_classes": tuned,
                         "l2": f"inputs larger than L2 ({RECORD_BYTES * n_tot / 1e9:.1f} GB of records)",
                         "policy": "exclusive", "parallelism": f"replicas x{world} (weak)",
                         "gen_s": round(t_gen, 1), "seed": rank_seed(gen.BASE_SEED + 4, rank, 1000),
