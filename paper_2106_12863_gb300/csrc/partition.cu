@@ -710,7 +710,7 @@ __device__ __forceinline__ uint32_t warp_exclusive(uint32_t v, uint32_t lane) {
     return incl - v;
 }
 
-// The group's thread 0: start the TMA copy of the page at list position j into buf[k].
+// One thread of the group: start the TMA copy of the page at list position j into buf[k].
 __device__ __forceinline__ void issue_page(const PartDev &p, const GroupSmem &gs, uint32_t j, uint32_t k) {
     const uint32_t id = p.page_list[j];
     const uint32_t fill = p.page_fill[id];
@@ -723,7 +723,7 @@ __device__ __forceinline__ void issue_page(const PartDev &p, const GroupSmem &gs
     if (bytes) bulk_g2s(smem_u32(gs.buf + k * kPartPage), p.pages + (uint64_t)id * kPartPage, bytes, bar);
 }
 
-// The group's thread 0: claim bucket b's next unsorted page and start its
+// One thread of the group: claim bucket b's next unsorted page and start its
 // copy into buf[k]. Returns its list position (the bucket's end or beyond
 // when every page is taken).
 __device__ __forceinline__ uint32_t claim_page(const PartDev &p, const GroupSmem &gs, uint32_t b, uint32_t k) {
